@@ -1,0 +1,432 @@
+"""Seeded synthetic inputs shared by the CPU oracle and the CUDA path.
+
+This module only builds *inputs*: boundary meshes, boundary-condition tags,
+the analytic data functions (as plain descriptors) and query point sets.
+It contains none of the walk-on-stars arithmetic, so both implementations can
+use it without sharing method code.
+
+Workload shapes follow the paper's experiments (Sec. 6): 2D polylines with a
+Dirichlet/Neumann split (Sec. 6.1, diffusion-curve problems), 3D closed meshes
+evaluated on a planar slice (Sec. 6.1, "solving on slices"), K = 8 lobes, dense
+evaluation grids.  The paper's own datasets are not used; every scene here is
+generated from a seed.
+
+Data-function descriptors (``Fn``) are an interface shared with both sides:
+``kind`` is one of the ``FN_*`` codes below and ``params`` a list of doubles.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+# ---- analytic data functions (codes are part of the C interface) ----------
+FN_ZERO = 0        # 0
+FN_CONST = 1       # params[0]
+FN_EXP_COS = 2     # exp(a x) cos(a y), a = params[0]
+FN_X2_MINUS_Y2 = 3  # x^2 - y^2
+FN_SQNORM = 4      # |x|^2                    (Laplacian 2d)
+FN_INV_DIST = 5    # 1/|x - c|, c = params[0:3] (harmonic in 3D)
+FN_LOG_DIST = 6    # log|x - c|, c = params[0:2] (harmonic in 2D)
+FN_GAUSS_SUM = 7   # sum_i A_i exp(-|x-p_i|^2/(2 s^2)); params = [n, s, A_1, p_1(3), ...]
+FN_COSH_COS = 8    # cosh(a x) cos(a y), a = params[0]
+
+BC_DIRICHLET = 0
+BC_NEUMANN = 1
+
+
+@dataclasses.dataclass
+class Fn:
+    kind: int = FN_ZERO
+    params: List[float] = dataclasses.field(default_factory=list)
+
+
+@dataclasses.dataclass
+class Scene:
+    """A closed boundary: ``prims`` index ``verts``; 2D segments run
+    counter-clockwise (domain on the left), 3D triangles wind
+    counter-clockwise seen from outside (outward normals)."""
+    name: str
+    dim: int
+    verts: np.ndarray          # (nv, dim) float64
+    prims: np.ndarray          # (np, dim) int32
+    bc: np.ndarray             # (np,) uint8, BC_DIRICHLET / BC_NEUMANN
+    g: Fn                      # Dirichlet data
+    f: Fn = dataclasses.field(default_factory=Fn)   # source term (Laplacian u = f)
+    h: Fn = dataclasses.field(default_factory=Fn)   # Neumann flux (zero only)
+    exact: Optional[Fn] = None  # closed-form solution when one exists
+    scene_id: int = 0
+
+    def __post_init__(self):
+        self.verts = np.ascontiguousarray(self.verts, dtype=np.float64)
+        self.prims = np.ascontiguousarray(self.prims, dtype=np.int32)
+        self.bc = np.ascontiguousarray(self.bc, dtype=np.uint8)
+
+    @property
+    def bbox(self):
+        return self.verts.min(0), self.verts.max(0)
+
+    def padded_bbox(self, pad=0.05):
+        lo, hi = self.bbox
+        ext = hi - lo
+        return lo - pad * ext, hi + pad * ext
+
+
+def eval_fn(fn: Fn, x: np.ndarray) -> np.ndarray:
+    """Evaluate a data descriptor on points (n, d) -- used by tests and the
+    bench to form closed-form references; not part of either solver."""
+    x = np.asarray(x, dtype=np.float64)
+    k, p = fn.kind, fn.params
+    if k == FN_ZERO:
+        return np.zeros(len(x))
+    if k == FN_CONST:
+        return np.full(len(x), p[0])
+    if k == FN_EXP_COS:
+        return np.exp(p[0] * x[:, 0]) * np.cos(p[0] * x[:, 1])
+    if k == FN_X2_MINUS_Y2:
+        return x[:, 0] ** 2 - x[:, 1] ** 2
+    if k == FN_SQNORM:
+        return (x ** 2).sum(1)
+    if k == FN_INV_DIST:
+        c = np.array(p[: x.shape[1]])
+        return 1.0 / np.linalg.norm(x - c, axis=1)
+    if k == FN_LOG_DIST:
+        c = np.array(p[: x.shape[1]])
+        return np.log(np.linalg.norm(x - c, axis=1))
+    if k == FN_COSH_COS:
+        return np.cosh(p[0] * x[:, 0]) * np.cos(p[0] * x[:, 1])
+    if k == FN_GAUSS_SUM:
+        n, s = int(p[0]), p[1]
+        out = np.zeros(len(x))
+        for i in range(n):
+            a = p[2 + 4 * i]
+            c = np.array(p[3 + 4 * i: 3 + 4 * i + x.shape[1]])
+            out += a * np.exp(-((x - c) ** 2).sum(1) / (2 * s * s))
+        return out
+    raise ValueError(f"unknown fn kind {k}")
+
+
+# ---- 2D scenes --------------------------------------------------------------
+
+def _closed_loop(n):
+    i = np.arange(n, dtype=np.int32)
+    return np.stack([i, (i + 1) % n], 1)
+
+
+def ngon(n: int = 64, radius: float = 1.0, g: Optional[Fn] = None, exact=True) -> Scene:
+    """Regular n-gon inscribed in a circle, all Dirichlet (64 segments,
+    g = e^x cos y is the small 2D Laplace workload)."""
+    th = 2 * np.pi * np.arange(n) / n
+    v = radius * np.stack([np.cos(th), np.sin(th)], 1)
+    g = g or Fn(FN_EXP_COS, [1.0])
+    return Scene(f"ngon{n}", 2, v, _closed_loop(n), np.zeros(n, np.uint8), g,
+                 exact=g if exact else None)
+
+
+def star_polyline(nseg: int = 4096, seed: int = 2, amp: float = 0.3, nmodes: int = 5,
+                  neumann_frac: float = 0.4, g: Optional[Fn] = None) -> Scene:
+    """Star-shaped polyline r(t) = 1 + amp * sum_j a_j cos(m_j t + phi_j) with
+    distinct m_j in 1..8, a_j ~ U(0,1) normalised to sum 1, phi_j ~ U(0, 2 pi);
+    a contiguous run of ``neumann_frac`` of the segments (seeded offset) is
+    zero-flux Neumann, the rest Dirichlet with g = x^2 - y^2."""
+    rng = np.random.default_rng(seed)
+    m = rng.choice(np.arange(1, 9), size=nmodes, replace=False)
+    a = rng.uniform(0, 1, nmodes)
+    a /= a.sum()
+    phi = rng.uniform(0, 2 * np.pi, nmodes)
+    th = 2 * np.pi * np.arange(nseg) / nseg
+    r = 1 + amp * (a[None, :] * np.cos(m[None, :] * th[:, None] + phi[None, :])).sum(1)
+    v = np.stack([r * np.cos(th), r * np.sin(th)], 1)
+    bc = np.zeros(nseg, np.uint8)
+    nn = int(round(neumann_frac * nseg))
+    off = int(rng.integers(0, nseg))
+    bc[(off + np.arange(nn)) % nseg] = BC_NEUMANN
+    return Scene(f"star{nseg}_s{seed}", 2, v, _closed_loop(nseg), bc,
+                 g or Fn(FN_X2_MINUS_Y2))
+
+
+def half_disk(narc: int = 64, nflat: int = 16, g: Optional[Fn] = None) -> Scene:
+    """Upper half of the unit disk: the flat edge on y = 0 is zero-flux
+    Neumann, the arc Dirichlet.  Any g with dg/dy = 0 on y = 0 (x^2 - y^2,
+    e^x cos y, |x|^2 for the Poisson case) is then the exact solution."""
+    th = np.pi * np.arange(narc + 1) / narc
+    arc = np.stack([np.cos(th), np.sin(th)], 1)          # (1,0) -> (-1,0) CCW
+    xs = -1 + 2 * np.arange(1, nflat) / nflat             # interior flat vertices
+    flat = np.stack([xs, np.zeros_like(xs)], 1)           # (-1,0) -> (1,0)
+    v = np.concatenate([arc, flat], 0)
+    n = len(v)
+    prims = _closed_loop(n)
+    bc = np.zeros(n, np.uint8)
+    bc[narc:] = BC_NEUMANN                                # segments from (-1,0) back to (1,0)
+    g = g or Fn(FN_X2_MINUS_Y2)
+    return Scene("half_disk", 2, v, prims, bc, g, exact=g)
+
+
+def rectangle_channel(nx: int = 16, ny: int = 8, a: float = math.pi) -> Scene:
+    """[-1,1] x [0,1]: the edges y = 0 and y = 1 are zero-flux Neumann, x = +-1
+    Dirichlet with g = cosh(a x) cos(a y), exact for a = pi (dg/dy = 0 on both
+    Neumann edges).  Walks bounce between two Neumann walls."""
+    pts = []
+    for i in range(nx):                       # bottom, left to right
+        pts.append((-1 + 2 * i / nx, 0.0))
+    for j in range(ny):                       # right, bottom to top
+        pts.append((1.0, j / ny))
+    for i in range(nx):                       # top, right to left
+        pts.append((1 - 2 * i / nx, 1.0))
+    for j in range(ny):                       # left, top to bottom
+        pts.append((-1.0, 1 - j / ny))
+    v = np.array(pts)
+    n = len(v)
+    bc = np.zeros(n, np.uint8)
+    bc[:nx] = BC_NEUMANN
+    bc[nx + ny: 2 * nx + ny] = BC_NEUMANN
+    g = Fn(FN_COSH_COS, [a])
+    return Scene("channel2d", 2, v, _closed_loop(n), bc, g, exact=g)
+
+
+# ---- 3D scenes --------------------------------------------------------------
+
+def icosphere(subdiv: int):
+    """Unit icosphere: 20 * 4^subdiv outward-wound triangles."""
+    t = (1 + 5 ** 0.5) / 2
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t),
+         (0, -1, -t), (0, 1, -t), (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+         (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+         (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    verts = [np.array(p, float) / np.linalg.norm(p) for p in v]
+    faces = f
+    for _ in range(subdiv):
+        cache = {}
+        new_faces = []
+
+        def mid(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in cache:
+                p = verts[a] + verts[b]
+                verts.append(p / np.linalg.norm(p))
+                cache[key] = len(verts) - 1
+            return cache[key]
+        for (a, b, c) in faces:
+            ab, bc_, ca = mid(a, b), mid(b, c), mid(c, a)
+            new_faces += [(a, ab, ca), (b, bc_, ab), (c, ca, bc_), (ab, bc_, ca)]
+        faces = new_faces
+    return np.array(verts), np.array(faces, np.int32)
+
+
+class Perlin3:
+    """Improved gradient noise (Perlin 2002 construction) with a seeded
+    permutation table; used only to displace generated meshes."""
+
+    _G = np.array([(1, 1, 0), (-1, 1, 0), (1, -1, 0), (-1, -1, 0), (1, 0, 1), (-1, 0, 1),
+                   (1, 0, -1), (-1, 0, -1), (0, 1, 1), (0, -1, 1), (0, 1, -1), (0, -1, -1)], float)
+
+    def __init__(self, seed: int):
+        rng = np.random.default_rng(seed)
+        p = rng.permutation(256)
+        self.p = np.concatenate([p, p]).astype(np.int64)
+        self.gi = rng.integers(0, 12, 256)
+
+    @staticmethod
+    def _fade(t):
+        return t * t * t * (t * (t * 6 - 15) + 10)
+
+    def __call__(self, x: np.ndarray) -> np.ndarray:
+        x = np.asarray(x, float)
+        i0 = np.floor(x).astype(np.int64)
+        fr = x - i0
+        i0 &= 255
+        u = self._fade(fr)
+        out = 0.0
+        for dx in (0, 1):
+            for dy in (0, 1):
+                for dz in (0, 1):
+                    h = self.p[self.p[self.p[i0[:, 0] + dx] + i0[:, 1] + dy] + i0[:, 2] + dz]
+                    g = self._G[self.gi[h & 255]]
+                    d = fr - np.array([dx, dy, dz], float)
+                    w = ((u[:, 0] if dx else 1 - u[:, 0]) * (u[:, 1] if dy else 1 - u[:, 1])
+                         * (u[:, 2] if dz else 1 - u[:, 2]))
+                    out = out + w * (g * d).sum(1)
+        return out
+
+
+def _cap_neumann(verts, prims, frac, axis):
+    cen = verts[prims].mean(1)
+    dirs = cen / np.linalg.norm(cen, axis=1, keepdims=True)
+    score = dirs @ axis
+    n = int(round(frac * len(prims)))
+    bc = np.zeros(len(prims), np.uint8)
+    bc[np.argsort(-score, kind="stable")[:n]] = BC_NEUMANN
+    return bc
+
+
+def displaced_icosphere(subdiv: int = 6, seed: int = 3, amp: float = 0.15, freq: float = 2.0,
+                        neumann_frac: float = 0.3, with_source: bool = True) -> Scene:
+    """Icosphere (20 * 4^subdiv triangles, 81,920 at subdiv 6) radially
+    displaced by amp * Perlin noise; the Neumann set is the 30% of faces
+    whose centroid direction best aligns with a seeded axis (one cap).
+    Dirichlet g = 1/|x - c|, c = (2.5, 0, 0); source = 4 seeded Gaussians
+    (sigma 0.1, amplitudes U(-4, 4), centres inside)."""
+    rng = np.random.default_rng(seed)
+    v, f = icosphere(subdiv)
+    noise = Perlin3(seed)
+    v = v * (1 + amp * noise(v * freq + 17.0))[:, None]
+    axis = rng.normal(size=3)
+    axis /= np.linalg.norm(axis)
+    bc = _cap_neumann(v, f, neumann_frac, axis)
+    src = Fn()
+    if with_source:
+        params = [4.0, 0.1]
+        for _ in range(4):
+            a = rng.uniform(-4, 4)
+            d = rng.normal(size=3)
+            c = d / np.linalg.norm(d) * rng.uniform(0, 0.5)
+            params += [a, *c]
+        src = Fn(FN_GAUSS_SUM, params)
+    return Scene(f"icosphere{subdiv}_s{seed}", 3, v, f, bc, Fn(FN_INV_DIST, [2.5, 0.0, 0.0]), f=src)
+
+
+def slab_box(n: int = 4) -> Scene:
+    """Box [-1,1]^2 x [0,1] triangulated with n x n quads per face; the
+    faces z = 0 and z = 1 are zero-flux Neumann, the side faces Dirichlet with
+    g = x^2 - y^2 (harmonic, z-independent, hence exact)."""
+    verts, tris, bcs = [], [], []
+
+    def face(origin, du, dv, neumann):
+        base = len(verts)
+        for j in range(n + 1):
+            for i in range(n + 1):
+                verts.append(origin + du * (i / n) + dv * (j / n))
+        for j in range(n):
+            for i in range(n):
+                a = base + j * (n + 1) + i
+                b, c, d = a + 1, a + n + 2, a + n + 1
+                tris.extend([(a, b, c), (a, c, d)])
+                bcs.extend([neumann, neumann])
+    O = np.array
+    # each face: du x dv points outward
+    face(O([-1., -1., 0.]), O([0., 2., 0.]), O([2., 0., 0.]), 1)   # z=0, normal -z
+    face(O([-1., -1., 1.]), O([2., 0., 0.]), O([0., 2., 0.]), 1)   # z=1, normal +z
+    face(O([-1., -1., 0.]), O([2., 0., 0.]), O([0., 0., 1.]), 0)   # y=-1, normal -y
+    face(O([-1., 1., 0.]), O([0., 0., 1.]), O([2., 0., 0.]), 0)    # y=+1, normal +y
+    face(O([-1., -1., 0.]), O([0., 0., 1.]), O([0., 2., 0.]), 0)   # x=-1, normal -x
+    face(O([1., -1., 0.]), O([0., 2., 0.]), O([0., 0., 1.]), 0)    # x=+1, normal +x
+    verts = np.array(verts)
+    # weld duplicate vertices so that edges are shared (needed for silhouettes)
+    key = np.round(verts * 1e9).astype(np.int64)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    verts = verts[first]
+    tris = inv.reshape(-1)[np.array(tris)]
+    g = Fn(FN_X2_MINUS_Y2)
+    return Scene("slab_box", 3, verts, tris.astype(np.int32), np.array(bcs, np.uint8), g, exact=g)
+
+
+def sphere_dirichlet(subdiv: int = 3, g: Optional[Fn] = None) -> Scene:
+    """Unit icosphere, all Dirichlet (g = 1/|x - c| with c outside is exact)."""
+    v, f = icosphere(subdiv)
+    g = g or Fn(FN_INV_DIST, [2.5, 0.0, 0.0])
+    return Scene(f"sphere{subdiv}", 3, v, f, np.zeros(len(f), np.uint8), g, exact=g)
+
+
+# ---- query point sets -------------------------------------------------------
+
+def grid_points_2d(n: int, lo, hi) -> np.ndarray:
+    """n x n cell centres of the box [lo, hi] (row-major, x fastest)."""
+    xs = lo[0] + (np.arange(n) + 0.5) / n * (hi[0] - lo[0])
+    ys = lo[1] + (np.arange(n) + 0.5) / n * (hi[1] - lo[1])
+    X, Y = np.meshgrid(xs, ys)
+    return np.stack([X.ravel(), Y.ravel()], 1)
+
+
+def slice_points_3d(n: int, lo, hi, z: float = 0.0) -> np.ndarray:
+    """n x n cell centres of the plane z = const over [lo, hi] in x, y."""
+    p2 = grid_points_2d(n, lo[:2], hi[:2])
+    return np.concatenate([p2, np.full((len(p2), 1), z)], 1)
+
+
+def inside_polygon_mask(scene: Scene, pts: np.ndarray) -> np.ndarray:
+    """Crossing-number test of 2D points against the scene polygon (input
+    masking only)."""
+    a = scene.verts[scene.prims[:, 0]]
+    b = scene.verts[scene.prims[:, 1]]
+    x, y = pts[:, 0:1], pts[:, 1:2]
+    cond = (a[None, :, 1] > y) != (b[None, :, 1] > y)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        xint = a[None, :, 0] + (y - a[None, :, 1]) * (b[None, :, 0] - a[None, :, 0]) / (b[None, :, 1] - a[None, :, 1])
+    cross = cond & (x < xint)
+    return (cross.sum(1) % 2) == 1
+
+
+def inside_polygon_mask_chunked(scene: Scene, pts: np.ndarray, chunk: int = 4096) -> np.ndarray:
+    out = np.zeros(len(pts), bool)
+    for s in range(0, len(pts), chunk):
+        out[s:s + chunk] = inside_polygon_mask(scene, pts[s:s + chunk])
+    return out
+
+
+def config_small_laplace():
+    """64-segment polyline approximating the unit circle, all Dirichlet,
+    g = e^x cos y; 32 x 32 grid of [-1,1]^2 clipped to the interior."""
+    sc = ngon(64)
+    pts = grid_points_2d(32, (-1, -1), (1, 1))
+    pts = pts[inside_polygon_mask(sc, pts)]
+    return sc, pts
+
+
+def config_star_guided(res: int = 512, nseg: int = 4096, seed: int = 2):
+    """4096-segment seeded star polyline, 40% zero-flux Neumann arc, Dirichlet
+    x^2 - y^2; res x res grid over the bounding box masked to the interior."""
+    sc = star_polyline(nseg, seed)
+    lo, hi = sc.bbox
+    pts = grid_points_2d(res, lo, hi)
+    pts = pts[inside_polygon_mask_chunked(sc, pts)]
+    return sc, pts
+
+
+def subsample(pts: np.ndarray, n: int, seed: int = 0) -> np.ndarray:
+    if n >= len(pts):
+        return pts
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(len(pts), n, replace=False))
+    return pts[idx]
+
+
+# ---- neural-field parameters for tests (exchange layout) ---------------------
+
+def random_field_params(dim: int, seed: int, lo, hi, K: int = 8, L: int = 16, log2T: int = 16,
+                        F: int = 2, H: int = 64, base_res: int = 16, max_res: Optional[int] = None,
+                        grid_scale: float = 0.5, w_scale: float = 1.0):
+    """Seeded field parameters in the exchange layout used by both
+    implementations: grid (L, 2^log2T, F), W1 (H, L*F), W2 (H, H),
+    W3 (nout, H), b3 (nout) with nout = (dim + 2) K + 1.  Returned as a dict
+    of float64 arrays plus the shape/box metadata."""
+    rng = np.random.default_rng(seed)
+    if max_res is None:
+        max_res = 2048 if dim == 2 else 512
+    T = 1 << log2T
+    nin = L * F
+    nout = (dim + 2) * K + 1
+    grid = rng.uniform(-grid_scale, grid_scale, (L, T, F))
+    W1 = rng.uniform(-1, 1, (H, nin)) * w_scale * math.sqrt(6.0 / nin)
+    W2 = rng.uniform(-1, 1, (H, H)) * w_scale * math.sqrt(6.0 / H)
+    W3 = rng.uniform(-1, 1, (nout, H)) * w_scale * math.sqrt(6.0 / H) * 0.5
+    b3 = rng.normal(size=nout) * 0.5
+    return dict(dim=dim, K=K, L=L, log2T=log2T, F=F, H=H, base_res=base_res, max_res=max_res,
+                lo=np.asarray(lo, float), hi=np.asarray(hi, float),
+                grid=grid, W1=W1, W2=W2, W3=W3, b3=b3)
+
+
+def round_to_bf16(a: np.ndarray) -> np.ndarray:
+    """Round float64 values to the nearest bfloat16 (ties to even) and return
+    them as float64 -- lets both implementations start from bit-identical
+    low-precision parameters."""
+    f = np.asarray(a, np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def round_to_fp16(a: np.ndarray) -> np.ndarray:
+    return np.asarray(a, np.float16).astype(np.float64)
