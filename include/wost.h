@@ -1,0 +1,237 @@
+/*
+ * libwost -- guided walk on stars on one GB300 (sm_103a).
+ *
+ * C ABI of the data-parallel hot path of "Guiding-Based Importance Sampling
+ * for Walk on Stars" (arXiv 2410.18944): batched walk-on-stars (WoSt) walks
+ * for the Poisson problem with mixed Dirichlet / zero-flux Neumann boundary
+ * (Sec. 3.1, Eq. linear_elliptic; estimator Sec. 3.2 Eq. wost_estm and its
+ * reparameterisation Sec. 4.1), with optional guided direction sampling from
+ * a von Mises-Fisher mixture decoded by a hash-grid + MLP neural field
+ * (Sec. 3.3, 4.2, 5.2), sample reflection at Neumann points (Sec. 4.3),
+ * one-sample MIS with a learnable selection probability (Sec. 4.4) and the
+ * online training step of the field (Sec. 4.2 Eq. one_sample_kld, Sec. 4.4
+ * Eq. one_sample_sp, Sec. 5.2 "Online Training Scheme").
+ *
+ * Conventions for every call:
+ *  - returns a wost_status; WOST_OK == 0.  On failure wost_last_error()
+ *    returns a message for the calling thread (thread-local, valid until the
+ *    next call on that thread).
+ *  - handles (wost_scene, wost_field) are opaque, owned by the library and
+ *    released with the matching *_destroy call.
+ *  - input arrays are owned by the caller and only read during the call;
+ *    no call keeps a caller pointer after it returns.
+ *  - "host-or-device" pointers are interpreted according to the
+ *    `*_on_device` flags of wost_exec; device pointers must be on the current
+ *    CUDA device.  Work is enqueued on wost_exec.stream (NULL = legacy
+ *    default stream) and the call synchronises that stream before returning
+ *    unless stated otherwise.
+ *  - geometry is stored in FP32, per-point accumulators in FP64.
+ *  - there is no CPU fallback: without a usable CUDA device every call that
+ *    needs one returns WOST_ERR_CUDA.
+ */
+#ifndef WOST_H
+#define WOST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WOST_OK = 0,
+    WOST_ERR_INVALID_ARG = 1,  /* null pointer, bad size, bad descriptor */
+    WOST_ERR_ILL_POSED = 2,    /* e.g. no Dirichlet primitive */
+    WOST_ERR_CUDA = 3,         /* CUDA runtime error (message has details) */
+    WOST_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    WOST_ERR_OOM = 5,          /* device allocation failed */
+    WOST_ERR_UNSUPPORTED = 6   /* valid but not implemented (e.g. h != 0) */
+} wost_status;
+
+/* Analytic data functions g (Dirichlet), f (source), h (Neumann flux).
+   kind codes:
+     0 zero            1 const p0              2 exp(p0 x) cos(p0 y)
+     3 x^2 - y^2       4 |x|^2                 5 1/|x - p[0:3]|
+     6 log|x - p[0:2]| 7 sum_i A_i exp(-|x - c_i|^2 / (2 s^2)),
+                         p = [n, s, A_1, c_1(3), A_2, c_2(3), ...], n <= 8
+     8 cosh(p0 x) cos(p0 y) */
+typedef struct {
+    int32_t kind;
+    int32_t nparams;
+    double params[40];
+} wost_fn;
+
+/* Boundary description (Sec. 3.1).  2D: prims are segments (2 vertex
+   indices), oriented counter-clockwise around the domain (domain on the left).
+   3D: prims are triangles (3 indices) wound counter-clockwise seen from
+   outside.  bc[i] = 0 Dirichlet, 1 Neumann.  The boundary must be closed. */
+typedef struct {
+    int32_t dim;               /* 2 or 3 */
+    int64_t nverts;
+    const double *verts;       /* host, nverts * dim */
+    int64_t nprims;
+    const int32_t *prims;      /* host, nprims * dim */
+    const uint8_t *bc;         /* host, nprims */
+    wost_fn g;                 /* Dirichlet data */
+    wost_fn f;                 /* source, Laplacian u = f */
+    wost_fn h;                 /* Neumann flux: must be zero (kind 0) */
+    uint32_t scene_id;         /* folded into the random-number key */
+} wost_scene_desc;
+
+typedef struct wost_scene wost_scene;
+typedef struct wost_field wost_field;
+
+/* Neural field of the guiding distribution (Sec. 5.2): L levels of a hash
+   grid (2^log2_table entries x F features, FP32 master + FP16 copy), MLP
+   (L F) -> H -> H -> (d + 2) K + 1 with ReLU, BF16 operands, FP32
+   accumulation.  Fixed in this build: F = 2, L * F = 32, H = 64, K = 8.
+   Positions are mapped to [0,1]^d by the box [lo, hi]. */
+typedef struct {
+    int32_t dim;
+    int32_t K;                 /* lobes (8) */
+    int32_t levels;            /* L (16) */
+    int32_t log2_table;        /* log2 of entries per level */
+    int32_t features;          /* F (2) */
+    int32_t hidden;            /* H (64) */
+    int32_t base_res, max_res; /* N_min, N_max of the level resolutions */
+    double lo[3], hi[3];
+    uint64_t seed;             /* initialisation */
+    float lr_grid, lr_mlp;     /* Adam learning rates */
+    float beta1, beta2, adam_eps;
+    float e_sel;               /* selection-loss fraction e (0.2, Sec. 4.4) */
+} wost_field_desc;
+
+/* Execution options of a solve. */
+typedef struct {
+    uint64_t seed;             /* walk random-number seed */
+    void *stream;              /* cudaStream_t, NULL = default stream */
+    int32_t points_on_device;  /* points pointer is device memory */
+    int32_t out_on_device;     /* out_mean / out_var are device memory */
+    int32_t c_mode;            /* 0 learned c = sigmoid(c'), 1 fixed c_fixed */
+    float c_fixed;
+    int32_t reflect;           /* 1 = sample reflection at Neumann (default) */
+    int32_t train;             /* guided: train the field after each batch */
+    int32_t train_until_wpp;   /* stop training after this many walks/point */
+    int64_t max_train_records; /* record buffer capacity (0 = default) */
+    int32_t walk_begin;        /* index of the first walk (RNG counter) */
+    int32_t ctas_per_sm;       /* launch shape override (0 = default) */
+} wost_exec;
+
+typedef struct {
+    int64_t walk_steps;        /* loop iterations of all walks, incl. terminal */
+    int64_t walks;
+    int64_t truncated;         /* walks closed by the maxsteps cap */
+    int64_t records;           /* training records produced */
+    int64_t records_dropped;   /* records beyond the buffer capacity */
+    int32_t train_steps;
+    float last_loss;
+    double ms_walk;            /* device time in walk kernels (CUDA events on the exec stream) */
+    double ms_train;           /* device time in training kernels (gradient + Adam + copies) */
+    int64_t kernel_launches;   /* kernels this call launched */
+    int64_t walk_launches;     /* of which walk kernels */
+    int64_t node_visits;       /* BVH nodes visited by all walk-step queries */
+    int64_t prim_visits;       /* primitives / silhouette elements tested */
+    double alg_bytes;          /* algorithmic bytes of the walk kernels: visited BVH nodes and
+                                  primitives, hash-grid corner reads, query points, FP64
+                                  accumulator updates, training-record writes and suffix pass */
+} wost_stats;
+
+const char *wost_last_error(void);
+/* fills *exec with the defaults (seed 1, reflect 1, train_until_wpp 256) */
+void wost_exec_defaults(wost_exec *exec);
+/* fills *desc with the defaults for dimension dim (K 8, L 16, F 2, H 64,
+   log2_table 16 in 2D / 19 in 3D, N_min 16, N_max 2048 / 512, lr 1e-2 grid /
+   1e-3 MLP, beta (0.9, 0.99), eps 1e-8, e 0.2); lo/hi = [-1, 1]^d */
+void wost_field_desc_defaults(wost_field_desc *desc, int32_t dim);
+
+/* Validates the boundary, builds three BVHs (Dirichlet closest point,
+   Neumann silhouette elements, Neumann ray cast; Sec. 5.3) on the host and
+   uploads them.  WOST_ERR_ILL_POSED if there is no Dirichlet primitive. */
+wost_status wost_create_scene(const wost_scene_desc *desc, wost_scene **out);
+wost_status wost_destroy_scene(wost_scene *scene);
+/* padded bounding box (5% of the extent on each side) for the field box */
+wost_status wost_scene_bbox(const wost_scene *scene, double lo[3], double hi[3]);
+
+/* Estimates u at npoints points (host-or-device, npoints * dim doubles)
+   with nwalks walks each (Sec. 3.2; guided: Sec. 4).  Points outside the
+   domain get NaN, points inside the eps-shell get g at the closest Dirichlet
+   point with variance 0.  out_mean[i] is the sample mean, out_var[i]
+   (nullable) the variance of that mean.  guided != 0 requires a field; with
+   exec->train the field is trained after every batch of one walk per point
+   (Sec. 5.2) until train_until_wpp walks per point.  Batches run in order,
+   so the estimate is deterministic up to floating-point atomics. */
+wost_status wost_solve(wost_scene *scene, wost_field *field, const double *points,
+                       int64_t npoints, int32_t nwalks, double eps, int32_t maxsteps,
+                       int32_t guided, double *out_mean, double *out_var, wost_stats *stats,
+                       const wost_exec *exec);
+
+/* Neural field lifetime and parameters (exchange layout, float32):
+   grid [L][2^log2_table][F], W1 [H][L F], W2 [H][H], W3 [nout][H], b3 [nout]
+   with nout = (dim + 2) K + 1; output order mu'_i (K x d), kappa'_i (K),
+   lambda'_i (K), c' (Tab. reg_map). */
+wost_status wost_create_field(const wost_field_desc *desc, wost_field **out);
+wost_status wost_destroy_field(wost_field *field);
+wost_status wost_field_set_params(wost_field *field, const float *grid, const float *W1,
+                                  const float *W2, const float *W3, const float *b3);
+wost_status wost_field_get_params(const wost_field *field, float *grid, float *W1, float *W2,
+                                  float *W3, float *b3);
+/* Raw network outputs (nout floats per point, host-or-device per exec) for
+   npoints points (npoints * dim doubles): hash-grid encoding + MLP on tensor
+   cores, the decode used inside the guided walk. */
+wost_status wost_field_decode(wost_field *field, const double *points, int64_t npoints,
+                              float *out_raw, const wost_exec *exec);
+
+/* One training step of the field (Sec. 4.2, 4.4) on the records of the most
+   recent guided batch of wost_solve (or those given by wost_train_records):
+   fused recomputation of the forward, loss gradients (Eq. one_sample_kld,
+   Eq. one_sample_sp), MLP backward on tensor cores, hash-grid scatter-add,
+   Adam.  *out_loss (nullable) receives the mean surrogate loss. */
+wost_status wost_train_step(wost_scene *scene, wost_field *field, const wost_exec *exec,
+                            float *out_loss);
+/* Replaces the field's record buffer with n caller records (12 floats each:
+   x[3], nu[3], n[3], on_neumann, q, target; host-or-device per exec). */
+wost_status wost_train_records(wost_field *field, const float *records, int64_t n,
+                               const wost_exec *exec);
+/* Copies up to cap records of the buffer to host memory; *n = count. */
+wost_status wost_get_records(const wost_field *field, float *records, int64_t cap, int64_t *n);
+/* Loss and gradients without the Adam update: grads in the exchange layout
+   (host), for checking against the FP64 reference. */
+wost_status wost_train_grad(wost_field *field, const wost_exec *exec, float *out_loss,
+                            float *g_grid, float *g_W1, float *g_W2, float *g_W3, float *g_b3);
+
+/* ---- query entry points (the walk's building blocks, for testing) ------- */
+/* closest Dirichlet primitive: index (-1 if none) and FP32 distance */
+wost_status wost_query_closest(wost_scene *scene, const double *points, int64_t n,
+                               int32_t *out_prim, float *out_dist);
+/* closest silhouette element of the Neumann boundary (Sec. 3.2): its vertex
+   (2D) or its edge's vertex pair a < b encoded a * nverts + b (3D), -1 if
+   none, and the distance (+inf if none) */
+wost_status wost_query_silhouette(wost_scene *scene, const double *points, int64_t n,
+                                  int64_t *out_elem, float *out_dist);
+/* first Neumann primitive hit along x + t v, 0 < t <= tmax, skipping prim
+   skip[i] (-1 none); -1 if no hit */
+wost_status wost_query_ray(wost_scene *scene, const double *org, const double *dir,
+                           const double *tmax, const int32_t *skip, int64_t n,
+                           int32_t *out_prim, float *out_t);
+/* vMF mixture: pdf at directions given identical parameters (mu K x d,
+   kappa K, lambda K per row) and one guided sample per row from Philox
+   counters (point, walk, step) with the walk's key; all host arrays. */
+wost_status wost_mixture_eval(int32_t dim, int32_t K, const float *mu, const float *kappa,
+                              const float *lambda, const float *nu, int64_t n, float *out_pdf);
+wost_status wost_mixture_sample(int32_t dim, int32_t K, const float *mu, const float *kappa,
+                                const float *lambda, const uint32_t *counters, uint64_t seed,
+                                uint32_t scene_id, int64_t n, float *out_nu, float *out_pdf);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+/* D[128 x N] = A[128 x K] B[N x K]^T (host float arrays, row-major) through
+   the library's tensor-core path (BF16 operands, FP32 accumulation); a_mn /
+   b_mn select K-major (0) or MN-major (1) shared-memory storage.  N in
+   [16, 256], K in [16, 128], both multiples of 16. */
+wost_status wost_diag_umma(int32_t a_mn, int32_t b_mn, int32_t N, int32_t K, const float *A, const float *B,
+                           float *D);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

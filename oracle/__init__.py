@@ -98,6 +98,8 @@ def _declare(L):
     L.orc_vmf2_sample_angle.restype = C.c_double
     L.orc_vmf2_sample_angle.argtypes = [C.c_double, _u32p, C.c_uint32, C.c_uint32, C.c_uint32, _ip]
     L.orc_vmf3_sample.argtypes = [C.c_double, _dp, C.c_double, C.c_double, _dp]
+    L.orc_guided_draw.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, C.c_double, _u32p, C.c_uint32, C.c_uint32,
+                                  C.c_uint32, _dp]
     L.orc_mixture_pdf.restype = C.c_double
     L.orc_mixture_pdf.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp]
     L.orc_field_nout.argtypes = [C.POINTER(_Field)]
@@ -263,6 +265,14 @@ def vmf3_sample(kappa, mu, xi, xi2):
     nu = np.zeros(3)
     lib().orc_vmf3_sample(float(kappa), _d(mu), float(xi), float(xi2), _d(nu))
     return nu
+
+
+def guided_draw(dim, mu, kappa, lam, c, key, pid, wid, step):
+    mu, kappa, lam = _f64(mu).ravel(), _f64(kappa), _f64(lam)
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    nu = np.zeros(3)
+    hit = lib().orc_guided_draw(dim, len(kappa), _d(mu), _d(kappa), _d(lam), float(c), k, pid, wid, step, _d(nu))
+    return hit, nu[:dim]
 
 
 def mixture_pdf(dim, mu, kappa, lam, nu):

@@ -107,6 +107,11 @@ typedef struct {
    x[3], nu[3], n[3], on_neumann, q (sampling pdf p~), target p_t */
 #define ORC_REC 12
 
+/* guided direction draw of one step (purpose-0 Philox draw, lobe pick,
+   vMF sample); returns 1 if the mixture branch was taken */
+int orc_guided_draw(int dim, int K, const double *mu, const double *kappa, const double *lambda, double c,
+                    const uint32_t key[2], uint32_t pid, uint32_t wid, uint32_t step, double *nu);
+
 /* status of a query point: 0 walk, 1 inside the epsilon-shell (value = g),
    2 outside the domain (value = NaN) */
 int orc_point_status(const orc_scene *s, const double *x, double eps, double *value);

@@ -86,6 +86,36 @@ static double beta22_inv(double u)
     return 0.5 + cos((acos(1 - 2 * u) + 4 * M_PI) / 3);
 }
 
+/* One-sample MIS direction (Sec. 4.4): with probability c (purpose-0 draw
+   u0) pick a lobe by the lambda-CDF (u1) and sample it (2D Best-Fisher with
+   purposes 3.., 3D from u2, u3); returns 1 and the direction if the mixture
+   was chosen, 0 (nu untouched) for the uniform branch. */
+int orc_guided_draw(int d, int K, const double *mu, const double *kap, const double *lam, double c,
+                    const uint32_t key[2], uint32_t pid, uint32_t wid, uint32_t step, double *nu)
+{
+    double u[4];
+    draw(key, pid, wid, step, 0, u);
+    if (!(u[0] < c)) return 0;
+    int lobe = K - 1;
+    double cdf = 0;
+    for (int i = 0; i < K; ++i) {
+        cdf += lam[i];
+        if (u[1] < cdf) {
+            lobe = i;
+            break;
+        }
+    }
+    const double *m = mu + lobe * d;
+    if (d == 2) {
+        double th = orc_vmf2_sample_angle(kap[lobe], key, pid, wid, step, NULL);
+        nu[0] = m[0] * cos(th) - m[1] * sin(th);
+        nu[1] = m[0] * sin(th) + m[1] * cos(th);
+    } else {
+        orc_vmf3_sample(kap[lobe], m, u[2], u[3], nu);
+    }
+    return 1;
+}
+
 typedef struct { double w, S; } step_info;
 
 double orc_walk(const orc_scene *s, const orc_field *fld, const orc_params *p, uint32_t pid,
@@ -140,28 +170,7 @@ double orc_walk(const orc_scene *s, const orc_field *fld, const orc_params *p, u
             orc_field_forward(fld, x, raw);
             orc_theta_map(fld, raw, mu, kap, lam, &c);
             if (p->c_mode == 1) c = p->c_fixed;
-            double u[4];
-            draw(key, pid, wid, (uint32_t)k, 0, u);
-            if (u[0] < c) {
-                from_guide = 1;
-                int lobe = K - 1;
-                double cdf = 0;
-                for (int i = 0; i < K; ++i) {
-                    cdf += lam[i];
-                    if (u[1] < cdf) {
-                        lobe = i;
-                        break;
-                    }
-                }
-                const double *m = mu + lobe * d;
-                if (d == 2) {
-                    double th = orc_vmf2_sample_angle(kap[lobe], key, pid, wid, (uint32_t)k, NULL);
-                    nu[0] = m[0] * cos(th) - m[1] * sin(th);
-                    nu[1] = m[0] * sin(th) + m[1] * cos(th);
-                } else {
-                    orc_vmf3_sample(kap[lobe], m, u[2], u[3], nu);
-                }
-            }
+            from_guide = orc_guided_draw(d, K, mu, kap, lam, c, key, pid, wid, (uint32_t)k, nu);
         }
         if (!from_guide) {
             double u[4];

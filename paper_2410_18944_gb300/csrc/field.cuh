@@ -1,0 +1,222 @@
+// Neural field of the guiding distribution (Sec. 4.2 Eq. nn_to_theta,
+// Sec. 5.2): multi-resolution hash-grid encoding (L = 16 levels, F = 2 FP16
+// features per lattice vertex, bi/tri-linear interpolation, levels
+// concatenated into 32 features) and a ReLU MLP 32 -> 64 -> 64 -> (d+2)K+1
+// whose three layers run on tcgen05 tensor cores: BF16 operands in shared
+// memory, FP32 accumulators in TMEM, one 128-row tile per 128 threads.
+//
+// Level l has resolution N_l = floor(N_min b^l) (N_{L-1} = N_max); levels
+// whose (N_l + 1)^d vertices fit the table are indexed densely, finer ones
+// by the spatial hash of Mueller et al. (2022) with primes 1, 2654435761,
+// 805459861.
+#pragma once
+#include "../../include/wost.h"
+#include "common.cuh"
+#include "umma.cuh"
+
+namespace wost {
+
+constexpr int kFeat = 32;     // L * F
+constexpr int kHid = 64;      // hidden width
+constexpr int kOutPad = 48;   // padded output width (33 in 2D, 41 in 3D)
+constexpr int kMaxLevels = 16;
+constexpr int kMaxK = 8;
+
+// bf16 weight image in shared memory (core-matrix tiles, rows = outputs)
+constexpr int kW1Bytes = kHid * kFeat * 2;       // 64 x 32
+constexpr int kW2Bytes = kHid * kHid * 2;        // 64 x 64
+constexpr int kW3Bytes = kOutPad * kHid * 2;     // 48 x 64
+constexpr int kWImgBytes = kW1Bytes + kW2Bytes + kW3Bytes;
+
+struct DevField {
+    int dim, K, L, log2T, nout;
+    uint32_t dense_mask;          // bit l: level l indexed densely
+    int res[kMaxLevels];
+    float lo[3], inv_ext[3];      // u = (x - lo) * inv_ext in [0,1]^d
+    const __half2 *grid16;        // L x 2^log2T entries (F = 2)
+    const uint4 *wimg;            // kWImgBytes, layout above
+    const float *b3;              // kOutPad (zero padded)
+};
+
+// interpolation corners of level l around x: T-table index and weight
+template <int D>
+__device__ __forceinline__ void level_corners(const DevField &f, int l, const float *u, uint32_t *idx, float *w) {
+    const int N = f.res[l];
+    const bool dense = (f.dense_mask >> l) & 1u;
+    const uint32_t mask = (1u << f.log2T) - 1u;
+    int c[3];
+    float fr[3];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        float p = u[k] * (float)N;
+        float fl = floorf(p);
+        fl = fminf(fmaxf(fl, 0.f), (float)(N - 1));
+        c[k] = (int)fl;
+        fr[k] = p - fl;
+    }
+#pragma unroll
+    for (int m = 0; m < (1 << D); ++m) {
+        uint32_t v[3];
+        float wt = 1.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            int b = (m >> k) & 1;
+            v[k] = (uint32_t)(c[k] + b);
+            wt *= b ? fr[k] : 1.f - fr[k];
+        }
+        uint32_t id;
+        if (dense) {
+            uint32_t side = (uint32_t)N + 1u;
+            id = v[0] + side * (v[1] + (D == 3 ? side * v[2] : 0u));
+        } else {
+            id = v[0] ^ (v[1] * 2654435761u);
+            if (D == 3) id ^= v[2] * 805459861u;
+            id &= mask;
+        }
+        idx[m] = id;
+        w[m] = wt;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void unit_coords(const DevField &f, const float *x, float *u) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) u[k] = (x[k] - f.lo[k]) * f.inv_ext[k];
+}
+
+// encode one position into a row of the bf16 feature tile (kFeat columns)
+template <int D>
+__device__ __forceinline__ void encode_row(const DevField &f, const float *x, uint8_t *xtile, int row) {
+    float u[D];
+    unit_coords<D>(f, x, u);
+    const size_t T = (size_t)1 << f.log2T;
+#pragma unroll 1
+    for (int l4 = 0; l4 < kMaxLevels; l4 += 4) {
+        float feat[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int l = l4 + j;
+            uint32_t idx[1 << D];
+            float w[1 << D];
+            level_corners<D>(f, l, u, idx, w);
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int m = 0; m < (1 << D); ++m) {
+                float2 g = __half22float2(__ldg(f.grid16 + (size_t)l * T + idx[m]));
+                a0 = fmaf(w[m], g.x, a0);
+                a1 = fmaf(w[m], g.y, a1);
+            }
+            feat[2 * j] = a0;
+            feat[2 * j + 1] = a1;
+        }
+        st_row8_bf16(xtile, row, 2 * l4, kFeat, feat);
+    }
+}
+
+// One 128-row tile: X (128 x 32) -> H1 -> H2 -> Y (128 x 48) in TMEM columns
+// [tcol, tcol + 64).  Called by all 128 threads of the tile; thread `row`
+// owns row `row`.  `issuer` issues the MMAs.  On return out[0..47] holds this
+// row's raw outputs (+ bias).  Returns false if a bounded wait timed out.
+struct TileCtx {
+    uint8_t *xtile;     // 128 x 32 bf16
+    uint8_t *htile;     // 128 x 64 bf16
+    const uint8_t *w;   // weight image
+    uint64_t *mbar;
+    uint32_t tmem;      // base column address of this tile (lane 0)
+    uint32_t phase;
+    int bar_id;         // named barrier of the tile (128 threads)
+};
+
+__device__ __forceinline__ bool tile_mma_wait(TileCtx &t, bool issuer, int which, int *err) {
+    // which: 0 = layer 1, 1 = layer 2, 2 = layer 3
+    fence_async_smem();
+    tc_fence_before();
+    named_sync(t.bar_id, 128);
+    if (issuer) {
+        tc_fence_after();
+        if (which == 0) umma_gemm(t.tmem, t.xtile, 0, kFeat, t.w, 0, kFeat, kHid, kFeat, false);
+        else if (which == 1) umma_gemm(t.tmem, t.htile, 0, kHid, t.w + kW1Bytes, 0, kHid, kHid, kHid, false);
+        else umma_gemm(t.tmem, t.htile, 0, kHid, t.w + kW1Bytes + kW2Bytes, 0, kHid, kOutPad, kHid, false);
+        umma_commit(t.mbar);
+    }
+    bool ok = mbar_wait_bounded(t.mbar, t.phase);
+    t.phase ^= 1u;
+    tc_fence_after();
+    // the give-up decision is taken by the whole tile, so that no thread is
+    // left alone at a later named barrier
+    ok = !named_or(t.bar_id, 128, !ok);
+    if (!ok && (threadIdx.x & 127) == 0) atomicOr(err, 2);
+    return ok;
+}
+
+__device__ __forceinline__ uint32_t lane_addr(uint32_t tmem, int row, int col) {
+    return tmem + ((uint32_t)(row & ~31) << 16) + (uint32_t)col;
+}
+
+// TMEM row -> ReLU -> bf16 row of the hidden tile
+__device__ __forceinline__ void hidden_epilogue(TileCtx &t, int row, float *keep /* nullable, 64 */) {
+#pragma unroll
+    for (int c = 0; c < kHid; c += 16) {
+        float v[16];
+        tmem_ld16(lane_addr(t.tmem, row, c), v);
+        tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+        if (keep)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) keep[c + i] = v[i];
+        st_row8_bf16(t.htile, row, c, kHid, v);
+        st_row8_bf16(t.htile, row, c + 8, kHid, v + 8);
+    }
+}
+
+__device__ __forceinline__ bool mlp_tile_forward(TileCtx &t, const DevField &f, int row, bool issuer, float *out,
+                                                 int *err) {
+    if (!tile_mma_wait(t, issuer, 0, err)) return false;
+    hidden_epilogue(t, row, nullptr);
+    if (!tile_mma_wait(t, issuer, 1, err)) return false;
+    hidden_epilogue(t, row, nullptr);
+    if (!tile_mma_wait(t, issuer, 2, err)) return false;
+#pragma unroll
+    for (int c = 0; c < kOutPad; c += 16) {
+        tmem_ld16(lane_addr(t.tmem, row, c), out + c);
+        tmem_ld_wait();
+    }
+#pragma unroll
+    for (int i = 0; i < kOutPad; ++i) out[i] += __ldg(f.b3 + i);
+    return true;
+}
+
+}  // namespace wost
+
+// host-side field state
+struct wost_field {
+    wost_field_desc desc{};
+    int nout = 0;
+    int64_t T = 0;
+    int res[16] = {0};
+    uint32_t dense_mask = 0;
+    // device buffers
+    float *grid32 = nullptr, *grid_m = nullptr, *grid_v = nullptr, *grid_g = nullptr;
+    __half2 *grid16 = nullptr;
+    float *mlp32 = nullptr, *mlp_m = nullptr, *mlp_v = nullptr, *mlp_g = nullptr;  // W1|W2|W3|b3 (exchange layout)
+    uint8_t *wimg = nullptr;
+    float *b3pad = nullptr;
+    int adam_t = 0;
+    // training records: final buffer (12 floats each) and per-slot scratch
+    float *rec = nullptr;
+    int64_t rec_cap = 0;
+    unsigned long long *rec_ctr = nullptr;   // [0] count, [1] dropped
+    float *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    float *loss_acc = nullptr;               // FP64 loss sum (8 bytes)
+    int t_c_mode = 0, t_reflect = 1;         // MIS options of the records in the buffer
+    float t_c_fixed = 0.5f;
+    int64_t n_mlp() const {
+        int H = desc.hidden, nin = desc.levels * desc.features;
+        return (int64_t)H * nin + (int64_t)H * H + (int64_t)nout * H + nout;
+    }
+    int64_t n_grid() const { return (int64_t)desc.levels * T * desc.features; }
+    wost::DevField dev() const;
+    ~wost_field();
+};

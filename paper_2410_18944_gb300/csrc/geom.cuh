@@ -1,0 +1,496 @@
+// Boundary queries of one walk step (Sec. 3.2, Sec. 5.3): closest Dirichlet
+// point (epsilon-shell test, R_D), closest Neumann silhouette (R_S), first
+// Neumann hit along a ray (next point on the star boundary).  Stack-based
+// traversal of a binary BVH with child boxes in the parent; node and
+// primitive loads are 16-byte vector loads through the read-only path.
+// Ties between equal distances go to the smaller original primitive id.
+#pragma once
+#include "common.cuh"
+
+namespace wost {
+
+constexpr int kStack = 64;
+
+// per-thread visit counts of the traversals (algorithmic-traffic accounting)
+struct Visits {
+    uint32_t nodes = 0, dprims = 0, sprims = 0, nprims = 0;
+};
+
+template <int D> struct NodeFloats;
+template <> struct NodeFloats<2> { static constexpr int n = 3; };
+template <> struct NodeFloats<3> { static constexpr int n = 4; };
+
+// squared distance from x to the two child boxes of a node
+template <int D>
+__device__ __forceinline__ void node_box_d2(const float4 *__restrict__ nodes, int node, const float *x,
+                                            float &d0, float &d1, int &r0, int &r1) {
+    if (D == 2) {
+        const float4 a = __ldg(nodes + 3 * node), b = __ldg(nodes + 3 * node + 1), r = __ldg(nodes + 3 * node + 2);
+        float ax = fmaxf(fmaxf(a.x - x[0], x[0] - a.z), 0.f), ay = fmaxf(fmaxf(a.y - x[1], x[1] - a.w), 0.f);
+        float bx = fmaxf(fmaxf(b.x - x[0], x[0] - b.z), 0.f), by = fmaxf(fmaxf(b.y - x[1], x[1] - b.w), 0.f);
+        d0 = ax * ax + ay * ay;
+        d1 = bx * bx + by * by;
+        r0 = __float_as_int(r.x);
+        r1 = __float_as_int(r.y);
+    } else {
+        const float4 a = __ldg(nodes + 4 * node), b = __ldg(nodes + 4 * node + 1);
+        const float4 c = __ldg(nodes + 4 * node + 2), r = __ldg(nodes + 4 * node + 3);
+        // child 0: lo = (a.x, a.y, a.z) hi = (a.w, b.x, b.y); child 1: lo = (b.z, b.w, c.x) hi = (c.y, c.z, c.w)
+        float ax = fmaxf(fmaxf(a.x - x[0], x[0] - a.w), 0.f);
+        float ay = fmaxf(fmaxf(a.y - x[1], x[1] - b.x), 0.f);
+        float az = fmaxf(fmaxf(a.z - x[2], x[2] - b.y), 0.f);
+        float bx = fmaxf(fmaxf(b.z - x[0], x[0] - c.y), 0.f);
+        float by = fmaxf(fmaxf(b.w - x[1], x[1] - c.z), 0.f);
+        float bz = fmaxf(fmaxf(c.x - x[2], x[2] - c.w), 0.f);
+        d0 = ax * ax + ay * ay + az * az;
+        d1 = bx * bx + by * by + bz * bz;
+        r0 = __float_as_int(r.x);
+        r1 = __float_as_int(r.y);
+    }
+}
+
+// entry/exit of the ray o + t v (inv = 1/v) with the two child boxes
+template <int D>
+__device__ __forceinline__ void node_box_ray(const float4 *__restrict__ nodes, int node, const float *o,
+                                             const float *inv, float tmax, float &t0, float &t1,
+                                             int &r0, int &r1) {
+    float lo0[3], hi0[3], lo1[3], hi1[3];
+    if (D == 2) {
+        const float4 a = __ldg(nodes + 3 * node), b = __ldg(nodes + 3 * node + 1), r = __ldg(nodes + 3 * node + 2);
+        lo0[0] = a.x; lo0[1] = a.y; hi0[0] = a.z; hi0[1] = a.w;
+        lo1[0] = b.x; lo1[1] = b.y; hi1[0] = b.z; hi1[1] = b.w;
+        r0 = __float_as_int(r.x);
+        r1 = __float_as_int(r.y);
+    } else {
+        const float4 a = __ldg(nodes + 4 * node), b = __ldg(nodes + 4 * node + 1);
+        const float4 c = __ldg(nodes + 4 * node + 2), r = __ldg(nodes + 4 * node + 3);
+        lo0[0] = a.x; lo0[1] = a.y; lo0[2] = a.z; hi0[0] = a.w; hi0[1] = b.x; hi0[2] = b.y;
+        lo1[0] = b.z; lo1[1] = b.w; lo1[2] = c.x; hi1[0] = c.y; hi1[1] = c.z; hi1[2] = c.w;
+        r0 = __float_as_int(r.x);
+        r1 = __float_as_int(r.y);
+    }
+    float e0 = 0.f, x0 = tmax, e1 = 0.f, x1 = tmax;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        float a0 = (lo0[k] - o[k]) * inv[k], b0 = (hi0[k] - o[k]) * inv[k];
+        float a1 = (lo1[k] - o[k]) * inv[k], b1 = (hi1[k] - o[k]) * inv[k];
+        e0 = fmaxf(e0, fminf(a0, b0));
+        x0 = fminf(x0, fmaxf(a0, b0));
+        e1 = fmaxf(e1, fminf(a1, b1));
+        x1 = fminf(x1, fmaxf(a1, b1));
+    }
+    t0 = e0 <= x0 ? e0 : __int_as_float(0x7f800000);
+    t1 = e1 <= x1 ? e1 : __int_as_float(0x7f800000);
+}
+
+// ---- primitive distances ----------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R seg_d2(R ax, R ay, R bx, R by, R px, R py, R &qx, R &qy) {
+    R ex = bx - ax, ey = by - ay;
+    R ee = ex * ex + ey * ey;
+    R t = ee > R(0) ? ((px - ax) * ex + (py - ay) * ey) / ee : R(0);
+    t = t < R(0) ? R(0) : (t > R(1) ? R(1) : t);
+    qx = ax + t * ex;
+    qy = ay + t * ey;
+    R dx = px - qx, dy = py - qy;
+    return dx * dx + dy * dy;
+}
+
+template <typename R>
+__device__ __forceinline__ R seg3_d2(const R *a, const R *b, const R *p) {
+    R e[3], ap[3], ee = 0, t = 0;
+    for (int i = 0; i < 3; ++i) { e[i] = b[i] - a[i]; ap[i] = p[i] - a[i]; ee += e[i] * e[i]; t += ap[i] * e[i]; }
+    t = ee > R(0) ? t / ee : R(0);
+    t = t < R(0) ? R(0) : (t > R(1) ? R(1) : t);
+    R s = 0;
+    for (int i = 0; i < 3; ++i) { R d = ap[i] - t * e[i]; s += d * d; }
+    return s;
+}
+
+// closest point on a triangle by Voronoi regions (Ericson 2004, Sec. 5.1.5)
+template <typename R>
+__device__ __forceinline__ R tri_d2(const R *a, const R *b, const R *c, const R *p, R *q) {
+    R ab[3], ac[3], ap[3], bp[3], cp[3];
+    for (int i = 0; i < 3; ++i) { ab[i] = b[i] - a[i]; ac[i] = c[i] - a[i]; ap[i] = p[i] - a[i]; bp[i] = p[i] - b[i]; cp[i] = p[i] - c[i]; }
+    auto dot = [](const R *u, const R *v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; };
+    R d1 = dot(ab, ap), d2 = dot(ac, ap);
+    R d3 = dot(ab, bp), d4 = dot(ac, bp);
+    R d5 = dot(ab, cp), d6 = dot(ac, cp);
+    R vc = d1 * d4 - d3 * d2, vb = d5 * d2 - d1 * d6, va = d3 * d6 - d5 * d4;
+    if (d1 <= R(0) && d2 <= R(0)) {
+        for (int i = 0; i < 3; ++i) q[i] = a[i];
+    } else if (d3 >= R(0) && d4 <= d3) {
+        for (int i = 0; i < 3; ++i) q[i] = b[i];
+    } else if (vc <= R(0) && d1 >= R(0) && d3 <= R(0)) {
+        R v = d1 / (d1 - d3);
+        for (int i = 0; i < 3; ++i) q[i] = a[i] + v * ab[i];
+    } else if (d6 >= R(0) && d5 <= d6) {
+        for (int i = 0; i < 3; ++i) q[i] = c[i];
+    } else if (vb <= R(0) && d2 >= R(0) && d6 <= R(0)) {
+        R w = d2 / (d2 - d6);
+        for (int i = 0; i < 3; ++i) q[i] = a[i] + w * ac[i];
+    } else if (va <= R(0) && (d4 - d3) >= R(0) && (d5 - d6) >= R(0)) {
+        R w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+        for (int i = 0; i < 3; ++i) q[i] = b[i] + w * (c[i] - b[i]);
+    } else {
+        R den = R(1) / (va + vb + vc);
+        R v = vb * den, w = vc * den;
+        for (int i = 0; i < 3; ++i) q[i] = a[i] + v * ab[i] + w * ac[i];
+    }
+    R s = 0;
+    for (int i = 0; i < 3; ++i) { R d = p[i] - q[i]; s += d * d; }
+    return s;
+}
+
+__device__ __forceinline__ void load_tri(const float4 *__restrict__ P, int s, float *a, float *b, float *c) {
+    float4 u = __ldg(P + 3 * s), v = __ldg(P + 3 * s + 1), w = __ldg(P + 3 * s + 2);
+    a[0] = u.x; a[1] = u.y; a[2] = u.z; b[0] = u.w; b[1] = v.x; b[2] = v.y; c[0] = v.z; c[1] = v.w; c[2] = w.x;
+}
+
+// ---- closest Dirichlet primitive -------------------------------------------
+// returns the leaf slot of the closest primitive (-1 if none); best = squared distance
+template <int D>
+__device__ int closest_dirichlet(const DevBVH &bv, const float *x, float &best, int *err, Visits *vis = nullptr) {
+    best = __int_as_float(0x7f800000);
+    if (bv.nprims == 0) return -1;
+    int best_slot = -1, best_id = 0x7fffffff;
+    int stack[kStack];
+    float sd[kStack];
+    int sp = 0, ref = 0;
+    for (;;) {
+        if (ref >= 0) {
+            float d0, d1;
+            int r0, r1;
+            node_box_d2<D>(bv.nodes, ref, x, d0, d1, r0, r1);
+            if (vis) vis->nodes++;
+            bool h0 = d0 <= best, h1 = d1 <= best;
+            if (h0 && h1) {
+                bool first0 = d0 <= d1;
+                if (sp < kStack) { stack[sp] = first0 ? r1 : r0; sd[sp] = first0 ? d1 : d0; ++sp; }
+                else atomicOr(err, 1);
+                ref = first0 ? r0 : r1;
+                continue;
+            } else if (h0) { ref = r0; continue; }
+            else if (h1) { ref = r1; continue; }
+        } else {
+            int s0 = leaf_start(ref), cnt = leaf_count(ref);
+            if (vis) vis->dprims += cnt;
+            for (int s = s0; s < s0 + cnt; ++s) {
+                float d2;
+                if (D == 2) {
+                    float4 p = __ldg(bv.prims + s);
+                    float qx, qy;
+                    d2 = seg_d2<float>(p.x, p.y, p.z, p.w, x[0], x[1], qx, qy);
+                } else {
+                    float a[3], b[3], c[3], q[3];
+                    load_tri(bv.prims, s, a, b, c);
+                    d2 = tri_d2<float>(a, b, c, x, q);
+                }
+                if (d2 <= best) {
+                    int id = __ldg(bv.ids + s);
+                    if (d2 < best || id < best_id) { best = d2; best_slot = s; best_id = id; }
+                }
+            }
+        }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (sd[sp] <= best) { ref = stack[sp]; found = true; break; }
+        }
+        if (!found) break;
+    }
+    return best_slot;
+}
+
+// FP64 distance (and closest point) from x to Dirichlet leaf slot s
+template <int D>
+__device__ __forceinline__ double dirichlet_dist64(const DevBVH &bv, int s, const float *x, double *q) {
+    double p[3] = {x[0], x[1], D == 3 ? x[2] : 0.0};
+    if (D == 2) {
+        const double *v = bv.prims64 + 4 * (size_t)s;
+        double d2 = seg_d2<double>(v[0], v[1], v[2], v[3], p[0], p[1], q[0], q[1]);
+        return sqrt(d2);
+    } else {
+        const double *v = bv.prims64 + 9 * (size_t)s;
+        return sqrt(tri_d2<double>(v, v + 3, v + 6, p, q));
+    }
+}
+
+// ---- closest silhouette ------------------------------------------------------
+// Silhouette rule: o = signed distance of x to the plane of an adjacent
+// Neumann primitive (positive on the domain side); front o > tau, back
+// o < -tau, edge-on otherwise; a silhouette has one neighbour seen from the
+// back and the other from the front or edge-on.  Elements flagged "always"
+// border the Neumann set.  Search radius starts at sqrt(best) (cap).
+__device__ __forceinline__ bool sil_rule(float o0, float o1, float tau) {
+    int c0 = o0 > tau ? 1 : (o0 < -tau ? -1 : 0);
+    int c1 = o1 > tau ? 1 : (o1 < -tau ? -1 : 0);
+    return (c0 == -1 && c1 >= 0) || (c1 == -1 && c0 >= 0);
+}
+
+// Normal-cone test of a silhouette-BVH child: no element below it can be a
+// silhouette from x when every normal in its cone (axis a, half-angle t) is
+// strictly front- or strictly back-facing from every point of its box.  With
+// c = x - (box centre), view half-angle p = asin(R / |c|) (R = box
+// half-diagonal), that holds when |a . c/|c|| > sin(t + p); the margin
+// tau / dist keeps every |o| above the edge-on tolerance.
+template <int D>
+__device__ __forceinline__ bool cone_prunes(float4 cone, const float *lo, const float *hi, const float *x,
+                                            float dist2, float tau) {
+    if (cone.w <= 0.f || dist2 <= 0.f) return false;
+    float c[3], r2 = 0.f, cl2 = 0.f, ac = 0.f;
+    const float ax[3] = {cone.x, cone.y, cone.z};
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        float h = 0.5f * (hi[k] - lo[k]);
+        c[k] = x[k] - 0.5f * (hi[k] + lo[k]);
+        r2 += h * h;
+        cl2 += c[k] * c[k];
+        ac += ax[k] * c[k];
+    }
+    if (cl2 <= r2) return false;
+    float inv = rsqrtf(cl2);
+    float sp = sqrtf(r2) * inv, cp = sqrtf(fmaxf(0.f, 1.f - sp * sp));
+    float ct = cone.w, st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
+    if (ct * cp - st * sp <= 0.f) return false;          // t + p >= 90 degrees
+    float s_tp = st * cp + ct * sp;                      // sin(t + p)
+    return fabsf(ac) * inv > s_tp + 2.f * tau * rsqrtf(dist2) + 1e-6f;
+}
+
+template <int D>
+__device__ __forceinline__ void child_boxes(const float4 *__restrict__ nodes, int node, float *lo0, float *hi0,
+                                            float *lo1, float *hi1) {
+    if (D == 2) {
+        const float4 a = __ldg(nodes + 3 * node), b = __ldg(nodes + 3 * node + 1);
+        lo0[0] = a.x; lo0[1] = a.y; hi0[0] = a.z; hi0[1] = a.w;
+        lo1[0] = b.x; lo1[1] = b.y; hi1[0] = b.z; hi1[1] = b.w;
+    } else {
+        const float4 a = __ldg(nodes + 4 * node), b = __ldg(nodes + 4 * node + 1), c = __ldg(nodes + 4 * node + 2);
+        lo0[0] = a.x; lo0[1] = a.y; lo0[2] = a.z; hi0[0] = a.w; hi0[1] = b.x; hi0[2] = b.y;
+        lo1[0] = b.z; lo1[1] = b.w; lo1[2] = c.x; hi1[0] = c.y; hi1[1] = c.z; hi1[2] = c.w;
+    }
+}
+
+template <int D>
+__device__ int closest_silhouette(const DevBVH &bv, const float *x, float tau, float &best, int *err,
+                                   Visits *vis = nullptr, const float4 *cones = nullptr) {
+    if (bv.nprims == 0) return -1;
+    int best_slot = -1, best_id = 0x7fffffff;
+    int stack[kStack];
+    float sd[kStack];
+    int sp = 0, ref = 0;
+    for (;;) {
+        if (ref >= 0) {
+            float d0, d1;
+            int r0, r1;
+            node_box_d2<D>(bv.nodes, ref, x, d0, d1, r0, r1);
+            if (vis) vis->nodes++;
+            bool h0 = d0 <= best, h1 = d1 <= best;
+            if (cones && (h0 || h1)) {
+                float lo0[3], hi0[3], lo1[3], hi1[3];
+                child_boxes<D>(bv.nodes, ref, lo0, hi0, lo1, hi1);
+                if (h0 && cone_prunes<D>(__ldg(cones + 2 * ref), lo0, hi0, x, d0, tau)) h0 = false;
+                if (h1 && cone_prunes<D>(__ldg(cones + 2 * ref + 1), lo1, hi1, x, d1, tau)) h1 = false;
+            }
+            if (h0 && h1) {
+                bool first0 = d0 <= d1;
+                if (sp < kStack) { stack[sp] = first0 ? r1 : r0; sd[sp] = first0 ? d1 : d0; ++sp; }
+                else atomicOr(err, 1);
+                ref = first0 ? r0 : r1;
+                continue;
+            } else if (h0) { ref = r0; continue; }
+            else if (h1) { ref = r1; continue; }
+        } else {
+            int s0 = leaf_start(ref), cnt = leaf_count(ref);
+            if (vis) vis->sprims += cnt;
+            for (int s = s0; s < s0 + cnt; ++s) {
+                float d2, o0, o1;
+                bool always;
+                if (D == 2) {
+                    float4 e0 = __ldg(bv.prims + 2 * s), e1 = __ldg(bv.prims + 2 * s + 1);
+                    float rx = x[0] - e0.x, ry = x[1] - e0.y;
+                    d2 = rx * rx + ry * ry;
+                    if (d2 > best) continue;
+                    o0 = e0.z * rx + e0.w * ry;
+                    o1 = e1.x * rx + e1.y * ry;
+                    always = e1.z != 0.f;
+                } else {
+                    float4 e0 = __ldg(bv.prims + 4 * s), e1 = __ldg(bv.prims + 4 * s + 1);
+                    float4 e2 = __ldg(bv.prims + 4 * s + 2), e3 = __ldg(bv.prims + 4 * s + 3);
+                    float a[3] = {e0.x, e0.y, e0.z}, b[3] = {e0.w, e1.x, e1.y};
+                    d2 = seg3_d2<float>(a, b, x);
+                    if (d2 > best) continue;
+                    float r[3] = {x[0] - a[0], x[1] - a[1], x[2] - a[2]};
+                    o0 = e1.z * r[0] + e1.w * r[1] + e2.x * r[2];
+                    o1 = e2.y * r[0] + e2.z * r[1] + e2.w * r[2];
+                    always = e3.x != 0.f;
+                }
+                if (!(always || sil_rule(o0, o1, tau))) continue;
+                int id = __ldg(bv.ids + s);
+                if (d2 < best || id < best_id) { best = d2; best_slot = s; best_id = id; }
+            }
+        }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (sd[sp] <= best) { ref = stack[sp]; found = true; break; }
+        }
+        if (!found) break;
+    }
+    return best_slot;
+}
+
+// ---- ray cast against Neumann primitives --------------------------------------
+template <int D>
+__device__ __forceinline__ bool ray_prim(const float4 *__restrict__ P, int s, const float *o, const float *v, float &t) {
+    if (D == 2) {
+        float4 p = __ldg(P + s);
+        float ex = p.z - p.x, ey = p.w - p.y;
+        float ax = p.x - o[0], ay = p.y - o[1];
+        float den = v[0] * ey - v[1] * ex;
+        if (den == 0.f) return false;
+        float tt = (ax * ey - ay * ex) / den;
+        float ss = (ax * v[1] - ay * v[0]) / den;
+        if (ss < 0.f || ss > 1.f || !(tt > 0.f)) return false;
+        t = tt;
+        return true;
+    } else {
+        float a[3], b[3], c[3];
+        load_tri(P, s, a, b, c);
+        float e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        float pv[3] = {v[1] * e2[2] - v[2] * e2[1], v[2] * e2[0] - v[0] * e2[2], v[0] * e2[1] - v[1] * e2[0]};
+        float det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
+        if (det == 0.f) return false;
+        float inv = 1.f / det;
+        float tv[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
+        float u = (tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2]) * inv;
+        if (u < 0.f || u > 1.f) return false;
+        float qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2], tv[0] * e1[1] - tv[1] * e1[0]};
+        float w = (v[0] * qv[0] + v[1] * qv[1] + v[2] * qv[2]) * inv;
+        if (w < 0.f || u + w > 1.f) return false;
+        float tt = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * inv;
+        if (!(tt > 0.f)) return false;
+        t = tt;
+        return true;
+    }
+}
+
+// FP64 re-test of a hit: the same intersection in double precision
+template <int D>
+__device__ __forceinline__ bool ray_prim64(const DevBVH &bv, int s, const float *of, const float *vf, double &t) {
+    double o[3] = {of[0], of[1], D == 3 ? of[2] : 0.0}, v[3] = {vf[0], vf[1], D == 3 ? vf[2] : 0.0};
+    if (D == 2) {
+        const double *p = bv.prims64 + 4 * (size_t)s;
+        double ex = p[2] - p[0], ey = p[3] - p[1], ax = p[0] - o[0], ay = p[1] - o[1];
+        double den = v[0] * ey - v[1] * ex;
+        if (den == 0.0) return false;
+        double tt = (ax * ey - ay * ex) / den, ss = (ax * v[1] - ay * v[0]) / den;
+        if (ss < 0.0 || ss > 1.0 || !(tt > 0.0)) return false;
+        t = tt;
+        return true;
+    } else {
+        const double *a = bv.prims64 + 9 * (size_t)s, *b = a + 3, *c = a + 6;
+        double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        double pv[3] = {v[1] * e2[2] - v[2] * e2[1], v[2] * e2[0] - v[0] * e2[2], v[0] * e2[1] - v[1] * e2[0]};
+        double det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
+        if (det == 0.0) return false;
+        double inv = 1.0 / det;
+        double tv[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
+        double u = (tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2]) * inv;
+        if (u < 0.0 || u > 1.0) return false;
+        double qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2], tv[0] * e1[1] - tv[1] * e1[0]};
+        double w = (v[0] * qv[0] + v[1] * qv[1] + v[2] * qv[2]) * inv;
+        if (w < 0.0 || u + w > 1.0) return false;
+        double tt = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * inv;
+        if (!(tt > 0.0)) return false;
+        t = tt;
+        return true;
+    }
+}
+
+// first Neumann hit with 0 < t <= tmax, skipping leaf slot `skip`; returns slot or -1
+template <int D>
+__device__ int ray_neumann(const DevBVH &bv, const float *o, const float *v, float tmax, int skip, float &thit,
+                           int *err, Visits *vis = nullptr) {
+    if (bv.nprims == 0) return -1;
+    float inv[3];
+#pragma unroll
+    for (int k = 0; k < D; ++k) inv[k] = 1.f / v[k];   // +-inf for a zero component is fine in the slab test
+    float best = tmax;
+    int best_slot = -1, best_id = 0x7fffffff;
+    int stack[kStack];
+    float st[kStack];
+    int sp = 0, ref = 0;
+    for (;;) {
+        if (ref >= 0) {
+            float t0, t1;
+            int r0, r1;
+            node_box_ray<D>(bv.nodes, ref, o, inv, best, t0, t1, r0, r1);
+            if (vis) vis->nodes++;
+            bool h0 = t0 <= best, h1 = t1 <= best;
+            if (h0 && h1) {
+                bool first0 = t0 <= t1;
+                if (sp < kStack) { stack[sp] = first0 ? r1 : r0; st[sp] = first0 ? t1 : t0; ++sp; }
+                else atomicOr(err, 1);
+                ref = first0 ? r0 : r1;
+                continue;
+            } else if (h0) { ref = r0; continue; }
+            else if (h1) { ref = r1; continue; }
+        } else {
+            int s0 = leaf_start(ref), cnt = leaf_count(ref);
+            if (vis) vis->nprims += cnt;
+            for (int s = s0; s < s0 + cnt; ++s) {
+                if (s == skip) continue;
+                float t;
+                if (ray_prim<D>(bv.prims, s, o, v, t) && t <= best) {
+                    int id = __ldg(bv.ids + s);
+                    if (t < best || id < best_id) { best = t; best_slot = s; best_id = id; }
+                }
+            }
+        }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (st[sp] <= best) { ref = stack[sp]; found = true; break; }
+        }
+        if (!found) break;
+    }
+    thit = best;
+    return best_slot;
+}
+
+// number of crossings of the ray o + t v (t > 0) with all primitives of a BVH
+template <int D>
+__device__ int ray_count(const DevBVH &bv, const float *o, const float *v, int *err) {
+    if (bv.nprims == 0) return 0;
+    float inv[3];
+#pragma unroll
+    for (int k = 0; k < D; ++k) inv[k] = 1.f / v[k];
+    const float big = 3.0e38f;
+    int cnt = 0, stack[kStack], sp = 0, ref = 0;
+    for (;;) {
+        if (ref >= 0) {
+            float t0, t1;
+            int r0, r1;
+            node_box_ray<D>(bv.nodes, ref, o, inv, big, t0, t1, r0, r1);
+            bool h0 = t0 <= big, h1 = t1 <= big;
+            if (h0 && h1) {
+                if (sp < kStack) stack[sp++] = r1; else atomicOr(err, 1);
+                ref = r0;
+                continue;
+            } else if (h0) { ref = r0; continue; }
+            else if (h1) { ref = r1; continue; }
+        } else {
+            int s0 = leaf_start(ref), c = leaf_count(ref);
+            for (int s = s0; s < s0 + c; ++s) {
+                float t;
+                cnt += ray_prim<D>(bv.prims, s, o, v, t) ? 1 : 0;
+            }
+        }
+        if (sp == 0) break;
+        ref = stack[--sp];
+    }
+    return cnt;
+}
+
+}  // namespace wost

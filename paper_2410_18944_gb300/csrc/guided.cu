@@ -1,0 +1,463 @@
+// Guided walk on stars (Sec. 4): per step, the walk's position is encoded by
+// the hash grid and decoded by the MLP on tcgen05 tensor cores into a vMF
+// mixture and a selection probability (Sec. 4.2, Tab. reg_map); the
+// direction is drawn by one-sample MIS between the mixture and the uniform
+// sphere (Sec. 4.4, Eq. mis_pdf), reflected below the tangent plane at
+// Neumann points (Sec. 4.3), and weighted by 1 / (|S| alpha p~) (Sec. 4.1).
+//
+// Persistent kernel, 256 threads = two 128-walk tiles per CTA sharing the
+// BF16 weight image in shared memory; each tile runs its own three-layer MMA
+// chain (accumulators in 64 TMEM columns, MMAs issued by one thread,
+// completion through an mbarrier) between named barriers, so the two tiles
+// of a CTA progress independently.  Finished walks are replaced from the
+// global work counter (warp-aggregated atomics) before every step.
+// Training records (Sec. 5.2): each guided step of a recorded walk stores
+// (x, nu, n, p~, weight, source term) in a per-thread scratch row; when the
+// walk ends a suffix pass turns them into targets |<u(x_{k+1})>|
+// (Sec. 4.1 Eq. guiding_dist) and appends them to the record buffer.
+#include <cstring>
+
+#include "field.cuh"
+#include "internal.h"
+#include "vmf.cuh"
+#include "walkstep.cuh"
+
+namespace wost {
+
+constexpr int kGuidedBlock = 256;
+constexpr int kXTileBytes = 128 * kFeat * 2;
+constexpr int kHTileBytes = 128 * kHid * 2;
+constexpr int kGuidedSmem = kWImgBytes + 2 * kXTileBytes + 2 * kHTileBytes + 64;
+constexpr int kRecFloats = 12;
+
+struct GuidedArgs {
+    WalkArgs w;
+    DevField f;
+    int c_mode;
+    float c_fixed;
+    int reflect;
+    int record;
+    float *scratch;               // [slot][maxsteps][12]
+    float *rec_out;               // [cap][12]
+    unsigned long long *rec_ctr;  // [0] count, [1] dropped
+    long long rec_cap;
+};
+
+// shared setup of a 256-thread CTA running two MLP tiles
+struct CtaTiles {
+    uint8_t *wimg, *xt, *ht;
+    uint64_t *mbar;
+    uint32_t *tptr;
+};
+
+__device__ __forceinline__ CtaTiles cta_tiles_setup(uint8_t *sm, const DevField &f) {
+    CtaTiles c;
+    c.wimg = sm;
+    c.xt = sm + kWImgBytes;
+    c.ht = c.xt + 2 * kXTileBytes;
+    c.mbar = reinterpret_cast<uint64_t *>(c.ht + 2 * kHTileBytes);
+    c.tptr = reinterpret_cast<uint32_t *>(c.mbar + 2);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kWImgBytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(c.wimg)[i] = __ldg(f.wimg + i);
+    if (tid == 0) {
+        mbar_init(&c.mbar[0], 1);
+        mbar_init(&c.mbar[1], 1);
+        fence_mbar_init();
+    }
+    if (tid < 32) tmem_alloc(c.tptr, 128);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return c;
+}
+
+__device__ __forceinline__ void cta_tiles_teardown(const CtaTiles &c) {
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(*c.tptr, 128);
+}
+
+__device__ __forceinline__ void zero_row(uint8_t *tile, int row, int C) {
+    for (int c = 0; c < C; c += 8) *reinterpret_cast<uint4 *>(tile + cm_offset(row, c, C)) = make_uint4(0, 0, 0, 0);
+}
+
+template <int D>
+__device__ __forceinline__ void end_recorded_walk(const GuidedArgs &g, int slot, int nrec, float term) {
+    float *base = g.scratch + (size_t)slot * g.w.maxsteps * kRecFloats;
+    unsigned long long at = atomicAdd(g.rec_ctr, (unsigned long long)nrec);
+    bool keep = (long long)(at + nrec) <= g.rec_cap;
+    if (!keep) atomicAdd(g.rec_ctr + 1, (unsigned long long)nrec);
+    float v = term;
+    for (int k = nrec - 1; k >= 0; --k) {
+        float4 *r = reinterpret_cast<float4 *>(base + (size_t)k * kRecFloats);
+        float4 a = r[0], b = r[1], c = r[2];   // x0 x1 x2 v0 | v1 v2 n0 n1 | n2 q w S
+        float tgt = fabsf(v);
+        v = c.z * v + c.w;
+        if (keep) {
+            float4 *o = reinterpret_cast<float4 *>(g.rec_out + (size_t)(at + k) * kRecFloats);
+            float onN = (b.z != 0.f || b.w != 0.f || c.x != 0.f) ? 1.f : 0.f;
+            o[0] = a;
+            o[1] = b;
+            o[2] = make_float4(c.x, onN, c.y, tgt);
+        }
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kGuidedBlock, 2) guided_walk_kernel(GuidedArgs g) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const WalkArgs &a = g.w;
+    CtaTiles ct = cta_tiles_setup(sm, g.f);
+    const int tid = threadIdx.x, tile = tid >> 7, row = tid & 127;
+    const bool issuer = row == 0;
+    TileCtx t{ct.xt + tile * kXTileBytes, ct.ht + tile * kHTileBytes, ct.wimg, &ct.mbar[tile],
+              *ct.tptr + (uint32_t)(tile * 64), 0u, 1 + tile};
+    const int slot = blockIdx.x * kGuidedBlock + tid;
+    const float area = D == 2 ? 2.f * WOST_PI : 4.f * WOST_PI;
+
+    Walk<D> w;
+    Visits vis;
+    bool active = false, exhausted = false;
+    unsigned long long nsteps = 0, ntrunc = 0, nwalks = 0;
+    for (;;) {
+        // one fetch attempt per iteration; no lane leaves or skips ahead, so the
+        // tile stays in step and re-converges at every named barrier
+        if (!active && !exhausted) {
+            unsigned long long item = warp_fetch_add(a.work_ctr, true);
+            if (item >= a.total) {
+                exhausted = true;
+            } else {
+                start_walk<D>(w, a, item);
+                if (a.status[w.pid] == 0) { active = true; nwalks++; }
+            }
+        }
+        if (!named_or(1 + tile, 128, active || !exhausted)) break;
+        bool live = active;
+        float r = 0.f, S = 0.f;
+        if (live) {
+            nsteps++;
+            float gv;
+            bool trunc = false;
+            if (step_geometry<D>(w, a, r, S, gv, trunc, &vis)) {
+                finish_walk(a, w.pid, w.acc);
+                if (g.record) end_recorded_walk<D>(g, slot, w.k, gv);
+                ntrunc += trunc;
+                active = live = false;
+            }
+        }
+        if (live) encode_row<D>(g.f, w.x, t.xtile, row);
+        else zero_row(t.xtile, row, kFeat);
+        float raw[kOutPad];
+        if (!mlp_tile_forward(t, g.f, row, issuer, raw, a.err)) break;
+        if (live) {
+            Mixture<D> m;
+            theta_map<D, 8>(raw, m);
+            const float c = g.c_mode ? g.c_fixed : m.c;
+            float nu[D];
+            bool from_guide = sample_direction<D, 8>(m, c, w.pid, w.wid, (uint32_t)w.k, a.key0, a.key1, nu);
+            const bool onN = w.prim >= 0;
+            bool zero_density = false;
+            if (onN) {
+                float dn = dotv<D>(nu, w.n);
+                if (dn < 0.f && (g.reflect || !from_guide)) { reflect<D>(nu, w.n); dn = -dn; }
+                zero_density = dn <= 0.f;   // Eq. angular_req: the recursive term is 0
+            }
+            if (zero_density) {
+                finish_walk(a, w.pid, w.acc);
+                if (g.record) end_recorded_walk<D>(g, slot, w.k, S);
+                active = false;
+            } else {
+                float pg = mixture_pdf<D, 8>(m, nu);
+                if (onN && g.reflect) {
+                    float nm[D];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) nm[i] = nu[i];
+                    reflect<D>(nm, w.n);
+                    pg += mixture_pdf<D, 8>(m, nm);
+                }
+                const float alpha = onN ? 0.5f : 1.f;
+                const float pu = (onN ? 2.f : 1.f) / area;
+                const float ptil = c * pg + (1.f - c) * pu;
+                // |S| alpha p_u == 1 exactly, so c = 0 gives weight 1 as in plain WoSt
+                const float wgt = 1.f / (c * area * alpha * pg + (1.f - c));
+                if (g.record) {
+                    float4 *rr = reinterpret_cast<float4 *>(g.scratch + ((size_t)slot * a.maxsteps + w.k) * kRecFloats);
+                    float n2 = onN && D == 3 ? w.n[D - 1] : 0.f;
+                    rr[0] = make_float4(w.x[0], w.x[1], D == 3 ? w.x[2] : 0.f, nu[0]);
+                    rr[1] = make_float4(nu[1], D == 3 ? nu[2] : 0.f, onN ? w.n[0] : 0.f, onN ? w.n[1] : 0.f);
+                    rr[2] = make_float4(n2, ptil, wgt, S);
+                }
+                w.T *= wgt;
+                step_move<D>(w, a, nu, r, &vis);
+            }
+        }
+    }
+    flush_counters(a, nsteps, ntrunc, nwalks, vis);
+    cta_tiles_teardown(ct);
+}
+
+// decode of arbitrary points: the same tile forward as inside the walk
+template <int D>
+__global__ void __launch_bounds__(kGuidedBlock, 1) decode_kernel(DevField f, const double *pts, int64_t n,
+                                                                 float *out, int nout, int *err) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    CtaTiles ct = cta_tiles_setup(sm, f);
+    const int tid = threadIdx.x, tile = tid >> 7, row = tid & 127;
+    TileCtx t{ct.xt + tile * kXTileBytes, ct.ht + tile * kHTileBytes, ct.wimg, &ct.mbar[tile],
+              *ct.tptr + (uint32_t)(tile * 64), 0u, 1 + tile};
+    for (int64_t base = (int64_t)blockIdx.x * kGuidedBlock; base < n; base += (int64_t)gridDim.x * kGuidedBlock) {
+        int64_t i = base + tid;
+        float x[D];
+        if (i < n) {
+            for (int k = 0; k < D; ++k) x[k] = (float)pts[i * D + k];
+            encode_row<D>(f, x, t.xtile, row);
+        } else {
+            zero_row(t.xtile, row, kFeat);
+        }
+        float raw[kOutPad];
+        if (!mlp_tile_forward(t, f, row, row == 0, raw, err)) break;
+        if (i < n)
+            for (int k = 0; k < nout; ++k) out[i * nout + k] = raw[k];
+    }
+    cta_tiles_teardown(ct);
+}
+
+// mixture pdf / samples for given (normalised) parameters
+template <int D>
+__global__ void mixture_eval_kernel(int K, const float *mu, const float *kap, const float *lam, const float *nu,
+                                    int64_t n, float *out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Mixture<D> m;
+    for (int j = 0; j < 8; ++j) {
+        bool on = j < K;
+        for (int k = 0; k < D; ++k) m.mu[j * D + k] = on ? mu[(i * K + j) * D + k] : 0.f;
+        m.kappa[j] = on ? kap[i * K + j] : 1.f;
+        m.lam[j] = on ? lam[i * K + j] : 0.f;
+        m.lognorm[j] = vmf_lognorm<D>(m.kappa[j]);
+    }
+    float v[D];
+    for (int k = 0; k < D; ++k) v[k] = nu[i * D + k];
+    out[i] = mixture_pdf<D, 8>(m, v);
+}
+
+template <int D>
+__global__ void mixture_sample_kernel(int K, const float *mu, const float *kap, const float *lam,
+                                      const uint32_t *ctr, uint32_t k0, uint32_t k1, int64_t n, float *onu,
+                                      float *opdf) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Mixture<D> m;
+    for (int j = 0; j < 8; ++j) {
+        bool on = j < K;
+        for (int k = 0; k < D; ++k) m.mu[j * D + k] = on ? mu[(i * K + j) * D + k] : 0.f;
+        m.kappa[j] = on ? kap[i * K + j] : 1.f;
+        m.lam[j] = on ? lam[i * K + j] : 0.f;
+        m.lognorm[j] = vmf_lognorm<D>(m.kappa[j]);
+    }
+    float v[D];
+    sample_direction<D, 8>(m, 1.f, ctr[3 * i], ctr[3 * i + 1], ctr[3 * i + 2], k0, k1, v);
+    for (int k = 0; k < D; ++k) onu[i * D + k] = v[k];
+    opdf[i] = mixture_pdf<D, 8>(m, v);
+}
+
+wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *loss_out_dev);
+
+int guided_ctas_per_sm() { return 1; }
+
+// resident CTAs per SM of the guided kernel (each holds 128 TMEM columns,
+// so at most 4 may share an SM)
+wost_status guided_occupancy(int dim, int *per_sm) {
+    static int occ[4] = {0, 0, 0, 0};
+    if (!occ[dim]) {
+        int n = 0;
+        if (dim == 2) {
+            WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGuidedSmem));
+            WOST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, guided_walk_kernel<2>, kGuidedBlock, kGuidedSmem));
+        } else {
+            WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGuidedSmem));
+            WOST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, guided_walk_kernel<3>, kGuidedBlock, kGuidedSmem));
+        }
+        occ[dim] = std::max(1, std::min(n, 4));
+    }
+    *per_sm = occ[dim];
+    return WOST_OK;
+}
+
+wost_status launch_guided(int dim, const GuidedArgs &g, int grid, cudaStream_t st) {
+    if (dim == 2) guided_walk_kernel<2><<<grid, kGuidedBlock, kGuidedSmem, st>>>(g);
+    else guided_walk_kernel<3><<<grid, kGuidedBlock, kGuidedSmem, st>>>(g);
+    WOST_CUDA(cudaGetLastError());
+    return WOST_OK;
+}
+
+wost_status ensure_records(wost_field *f, int64_t cap, size_t scratch_bytes);
+
+wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, const wost_exec &ex,
+                         cudaStream_t st, wost_stats *stats, int walk_begin, CallTiming &tm) {
+    if (f->desc.dim != s->dim) { set_error("wost_solve: field dimension differs from the scene"); return WOST_ERR_INVALID_ARG; }
+    GuidedArgs g{};
+    g.f = f->dev();
+    g.c_mode = ex.c_mode;
+    g.c_fixed = ex.c_fixed;
+    g.reflect = ex.reflect;
+    f->t_c_mode = ex.c_mode;
+    f->t_c_fixed = ex.c_fixed;
+    f->t_reflect = ex.reflect;
+    int occ = 1;
+    wost_status orc = guided_occupancy(s->dim, &occ);
+    if (orc != WOST_OK) return orc;
+    int cps = ex.ctas_per_sm > 0 ? std::min(ex.ctas_per_sm, occ) : occ;
+    int grid = num_sms() * cps;
+    const bool any_train = ex.train && walk_begin < ex.train_until_wpp;
+    if (any_train) {
+        int64_t cap = ex.max_train_records > 0 ? ex.max_train_records : std::max<int64_t>(a.npoints * 64, 1 << 20);
+        size_t scratch = (size_t)grid * kGuidedBlock * (size_t)std::max(a.maxsteps, 1) * kRecFloats * sizeof(float);
+        wost_status rc = ensure_records(f, cap, scratch);
+        if (rc != WOST_OK) return rc;
+    }
+    g.scratch = f->scratch;
+    g.rec_out = f->rec;
+    g.rec_ctr = f->rec_ctr;
+    g.rec_cap = f->rec_cap;
+    int ntrain = 0;
+    for (int b = 0; b < nwalks; ++b) {
+        g.w = a;
+        g.w.walk_begin = walk_begin + b;
+        g.w.total = (unsigned long long)a.npoints;
+        g.record = ex.train && (walk_begin + b) < ex.train_until_wpp;
+        WOST_CUDA(cudaMemsetAsync(a.work_ctr, 0, sizeof(unsigned long long), st));
+        if (g.record) WOST_CUDA(cudaMemsetAsync(f->rec_ctr, 0, 2 * sizeof(unsigned long long), st));
+        g.f = f->dev();
+        tm.mark(tm.walk, st);
+        wost_status rc = launch_guided(s->dim, g, grid, st);
+        tm.mark(tm.walk, st);
+        tm.launches++;
+        tm.walk_launches++;
+        if (rc != WOST_OK) return rc;
+        if (g.record) {
+            tm.mark(tm.train, st);
+            rc = train_launch(f, s->dim, st, true, nullptr);
+            tm.mark(tm.train, st);
+            tm.launches += 5;   // gradient, 2 x Adam, FP16 grid copy, BF16 weight image
+            if (rc != WOST_OK) return rc;
+            ntrain++;
+        }
+    }
+    if (stats) {
+        stats->train_steps = ntrain;
+        if (ntrain) {
+            unsigned long long c[2];
+            WOST_CUDA(cudaMemcpyAsync(c, f->rec_ctr, sizeof(c), cudaMemcpyDeviceToHost, st));
+            WOST_CUDA(cudaStreamSynchronize(st));
+            stats->records = (int64_t)c[0];
+            stats->records_dropped = (int64_t)c[1];
+        }
+    }
+    return WOST_OK;
+}
+
+}  // namespace wost
+
+using namespace wost;
+
+extern "C" wost_status wost_field_decode(wost_field *f, const double *points, int64_t n, float *out_raw,
+                                         const wost_exec *exec) {
+    if (!f || n < 0 || (n > 0 && (!points || !out_raw))) { set_error("wost_field_decode: invalid argument"); return WOST_ERR_INVALID_ARG; }
+    if (n == 0) return WOST_OK;
+    wost_exec ex;
+    if (exec) ex = *exec; else wost_exec_defaults(&ex);
+    cudaStream_t st = (cudaStream_t)ex.stream;
+    const int D = f->desc.dim;
+    double *dp = const_cast<double *>(points);
+    float *dout = out_raw;
+    bool own_p = false, own_o = false;
+    if (!ex.points_on_device) {
+        WOST_CUDA(cudaMalloc(&dp, n * D * sizeof(double)));
+        own_p = true;
+        WOST_CUDA(cudaMemcpyAsync(dp, points, n * D * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    if (!ex.out_on_device) {
+        WOST_CUDA(cudaMalloc(&dout, n * f->nout * sizeof(float)));
+        own_o = true;
+    }
+    int grid = (int)std::min<int64_t>((n + kGuidedBlock - 1) / kGuidedBlock, (int64_t)num_sms() * 2);
+    if (D == 2) {
+        WOST_CUDA(cudaFuncSetAttribute(decode_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGuidedSmem));
+        decode_kernel<2><<<grid, kGuidedBlock, kGuidedSmem, st>>>(f->dev(), dp, n, dout, f->nout, device_err_flag());
+    } else {
+        WOST_CUDA(cudaFuncSetAttribute(decode_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGuidedSmem));
+        decode_kernel<3><<<grid, kGuidedBlock, kGuidedSmem, st>>>(f->dev(), dp, n, dout, f->nout, device_err_flag());
+    }
+    WOST_CUDA(cudaGetLastError());
+    if (own_o) WOST_CUDA(cudaMemcpyAsync(out_raw, dout, n * f->nout * sizeof(float), cudaMemcpyDeviceToHost, st));
+    WOST_CUDA(cudaStreamSynchronize(st));
+    if (own_p) cudaFree(dp);
+    if (own_o) cudaFree(dout);
+    return device_check(st);
+}
+
+namespace {
+wost_status mixture_common(int dim, int K, int64_t n, const float *mu, const float *kappa, const float *lambda,
+                           float **dmu, float **dk, float **dl) {
+    if ((dim != 2 && dim != 3) || K < 1 || K > 8 || n < 0 || (n > 0 && (!mu || !kappa || !lambda))) {
+        set_error("wost_mixture: invalid argument");
+        return WOST_ERR_INVALID_ARG;
+    }
+    WOST_CUDA(cudaMalloc(dmu, std::max<int64_t>(n, 1) * K * dim * sizeof(float)));
+    WOST_CUDA(cudaMalloc(dk, std::max<int64_t>(n, 1) * K * sizeof(float)));
+    WOST_CUDA(cudaMalloc(dl, std::max<int64_t>(n, 1) * K * sizeof(float)));
+    WOST_CUDA(cudaMemcpy(*dmu, mu, n * K * dim * sizeof(float), cudaMemcpyHostToDevice));
+    WOST_CUDA(cudaMemcpy(*dk, kappa, n * K * sizeof(float), cudaMemcpyHostToDevice));
+    WOST_CUDA(cudaMemcpy(*dl, lambda, n * K * sizeof(float), cudaMemcpyHostToDevice));
+    return WOST_OK;
+}
+}  // namespace
+
+extern "C" wost_status wost_mixture_eval(int32_t dim, int32_t K, const float *mu, const float *kappa,
+                                         const float *lambda, const float *nu, int64_t n, float *out_pdf) {
+    if (n > 0 && (!nu || !out_pdf)) { set_error("wost_mixture_eval: null argument"); return WOST_ERR_INVALID_ARG; }
+    float *dmu = nullptr, *dk = nullptr, *dl = nullptr, *dn = nullptr, *dout = nullptr;
+    wost_status rc = mixture_common(dim, K, n, mu, kappa, lambda, &dmu, &dk, &dl);
+    if (rc != WOST_OK || n == 0) { cudaFree(dmu); cudaFree(dk); cudaFree(dl); return rc; }
+    cudaError_t e = cudaMalloc(&dn, n * dim * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dout, n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(dn, nu, n * dim * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        int bs = 128, gr = (int)((n + bs - 1) / bs);
+        if (dim == 2) mixture_eval_kernel<2><<<gr, bs>>>(K, dmu, dk, dl, dn, n, dout);
+        else mixture_eval_kernel<3><<<gr, bs>>>(K, dmu, dk, dl, dn, n, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out_pdf, dout, n * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaFree(dmu); cudaFree(dk); cudaFree(dl); cudaFree(dn); cudaFree(dout);
+    return e == cudaSuccess ? WOST_OK : cuda_status(e, "wost_mixture_eval");
+}
+
+extern "C" wost_status wost_mixture_sample(int32_t dim, int32_t K, const float *mu, const float *kappa,
+                                           const float *lambda, const uint32_t *counters, uint64_t seed,
+                                           uint32_t scene_id, int64_t n, float *out_nu, float *out_pdf) {
+    if (n > 0 && (!counters || !out_nu || !out_pdf)) { set_error("wost_mixture_sample: null argument"); return WOST_ERR_INVALID_ARG; }
+    float *dmu = nullptr, *dk = nullptr, *dl = nullptr, *dnu = nullptr, *dpdf = nullptr;
+    uint32_t *dc = nullptr;
+    wost_status rc = mixture_common(dim, K, n, mu, kappa, lambda, &dmu, &dk, &dl);
+    if (rc != WOST_OK || n == 0) { cudaFree(dmu); cudaFree(dk); cudaFree(dl); return rc; }
+    cudaError_t e = cudaMalloc(&dc, n * 3 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&dnu, n * dim * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dpdf, n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(dc, counters, n * 3 * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        int bs = 128, gr = (int)((n + bs - 1) / bs);
+        uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32) + scene_id;
+        if (dim == 2) mixture_sample_kernel<2><<<gr, bs>>>(K, dmu, dk, dl, dc, k0, k1, n, dnu, dpdf);
+        else mixture_sample_kernel<3><<<gr, bs>>>(K, dmu, dk, dl, dc, k0, k1, n, dnu, dpdf);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out_nu, dnu, n * dim * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(out_pdf, dpdf, n * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaFree(dmu); cudaFree(dk); cudaFree(dl); cudaFree(dc); cudaFree(dnu); cudaFree(dpdf);
+    return e == cudaSuccess ? WOST_OK : cuda_status(e, "wost_mixture_sample");
+}

@@ -1,0 +1,429 @@
+// Online training step of the guiding field (Sec. 4.2, 4.4, 5.2).
+//
+// Per record (x, nu, Neumann normal n, q = p~ at sampling, target p_t) the
+// surrogate loss
+//   l = -(p_t / q) [ log p_g(nu | Theta(x)) + e log(c p_g0 + (1 - c) p_u) ]
+// (p_g0 = p_g held constant) has exactly the paper's one-sample gradients:
+// Eq. one_sample_kld for Theta and Eq. one_sample_sp for c.  The mean over
+// records is back-propagated through the MLP and scattered onto the hash grid.
+//
+// One fused persistent kernel, two 128-record tiles per CTA (256 threads):
+//   forward recomputation (3 tcgen05 MMAs) -> per-thread loss and d raw ->
+//   dH2 = dY W3, dZ2 = dH2 * [H2 > 0] -> dH1 = dZ2 W2 -> dZ1 -> dX = dZ1 W1
+//   -> hash-grid scatter-add (FP32 atomics); the weight gradients
+//   dW3 = dY^T H2, dW2 = dZ2^T H1, dW1 = dZ1^T X accumulate in TMEM across all
+//   tiles of the CTA (MN-major operands read the same per-record tiles) and
+//   are flushed once with atomics.  Activations are recomputed, not stored.
+// Then one elementwise Adam kernel (Kingma & Ba 2015) updates the FP32
+// masters and rewrites the FP16 grid and BF16 weight-image copies.
+#include <cstring>
+
+#include "field.cuh"
+#include "internal.h"
+#include "vmf.cuh"
+
+namespace wost {
+
+constexpr int kTrainBlock = 256;
+constexpr int kTX = 128 * kFeat * 2;     // X tile
+constexpr int kTH = 128 * kHid * 2;      // H1 / H2 tiles
+constexpr int kTG = 128 * 128 * 2;       // G tile: [dY | dZ2] then [dZ1 | dZ2]
+// gradient tiles are stored as a BF16 pair hi + lo (lo = bf16(v - hi)), so the
+// MMAs see the FP32 gradient to ~16 bits; activations and weights are BF16
+// exactly as in the forward pass
+constexpr int kTileBytes = kTX + 2 * kTH + 2 * kTG;
+constexpr int kTrainSmem = kWImgBytes + 2 * kTileBytes + 64;
+
+struct TrainArgs {
+    DevField f;
+    const float *rec;
+    const unsigned long long *rec_ctr;
+    long long rec_cap;
+    int c_mode;
+    float c_fixed;
+    int reflect;
+    float e_sel;
+    float *g_grid;   // L x T x F
+    float *g_W1, *g_W2, *g_W3, *g_b3;
+    double *loss_acc;
+    int *err;
+};
+
+struct TTile {
+    uint8_t *X, *H1, *H2, *G, *Gl;
+    const uint8_t *w;
+    uint64_t *mbar;
+    uint32_t s0, acc3, acc2, acc1;   // TMEM column addresses
+    uint32_t phase;
+    int bar;
+};
+
+template <class F>
+__device__ __forceinline__ bool tt_issue_wait(TTile &t, bool issuer, F issue, int *err) {
+    fence_async_smem();
+    tc_fence_before();
+    named_sync(t.bar, 128);
+    if (issuer) {
+        tc_fence_after();
+        issue();
+        umma_commit(t.mbar);
+    }
+    bool ok = mbar_wait_bounded(t.mbar, t.phase);
+    t.phase ^= 1u;
+    tc_fence_after();
+    ok = !named_or(t.bar, 128, !ok);   // tile-uniform give-up decision
+    if (!ok && (threadIdx.x & 127) == 0) atomicOr(err, 2);
+    return ok;
+}
+
+// 8 values of a row as a BF16 hi/lo pair into the G tiles
+__device__ __forceinline__ void st_row8_split(uint8_t *hi, uint8_t *lo, int r, int c8, int C, const float *v) {
+    float h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        h[i] = __bfloat162float(__float2bfloat16_rn(v[i]));
+        l[i] = v[i] - h[i];
+    }
+    st_row8_bf16(hi, r, c8, C, h);
+    st_row8_bf16(lo, r, c8, C, l);
+}
+
+__device__ __forceinline__ void ld_cols(uint32_t taddr, int row, int ncols, float *v) {
+    for (int c = 0; c < ncols; c += 16) {
+        tmem_ld16(lane_addr(taddr, row, c), v + c);
+        tmem_ld_wait();
+    }
+}
+
+// loss and gradient w.r.t. the raw outputs for one record
+template <int D>
+__device__ __forceinline__ float record_grad(const TrainArgs &a, const float *rec, const float *raw, float inv_n,
+                                             float *draw) {
+    const int K = 8;
+    Mixture<D> m;
+    theta_map<D, 8>(raw, m);
+    const float c = a.c_mode ? a.c_fixed : m.c;
+    float nu[2][3], nrm[3];
+    for (int i = 0; i < 3; ++i) { nu[0][i] = rec[3 + i]; nrm[i] = rec[6 + i]; }
+    const bool onN = rec[9] != 0.f;
+    const float q = rec[10], pt = rec[11];
+    int nd = 1;
+    if (onN && a.reflect) {
+        float t = 2.f * (nu[0][0] * nrm[0] + nu[0][1] * nrm[1] + (D == 3 ? nu[0][2] * nrm[2] : 0.f));
+        for (int i = 0; i < D; ++i) nu[1][i] = nu[0][i] - t * nrm[i];
+        nd = 2;
+    }
+    float v[2][8], pg = 0.f;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        float s = 0.f;
+        for (int d2 = 0; d2 < nd; ++d2) {
+            v[d2][j] = __expf(m.lognorm[j] - m.kappa[j] * half_dist2<D>(m.mu + j * D, nu[d2]));
+            s += v[d2][j];
+        }
+        pg += m.lam[j] * s;
+    }
+    const float area = D == 2 ? 2.f * WOST_PI : 4.f * WOST_PI;
+    const float pu = (onN ? 2.f : 1.f) / area;
+    const float ptil = c * pg + (1.f - c) * pu;
+    for (int i = 0; i < kOutPad; ++i) draw[i] = 0.f;
+    if (!(pt > 0.f) || !(q > 0.f)) return 0.f;
+    const float wt = pt / q;
+    const float pgs = fmaxf(pg, 1e-30f);
+    float loss = -wt * (__logf(pgs) + (a.c_mode == 0 ? a.e_sel * __logf(ptil) : 0.f));
+    const float dpg = -wt / pgs * inv_n;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const float *mu = m.mu + j * D;
+        float sj = 0.f, dk = 0.f, dm[3] = {0.f, 0.f, 0.f};
+        const float A = vmf_mean_cos<D>(m.kappa[j]);
+        for (int d2 = 0; d2 < nd; ++d2) {
+            float cm = 0.f;
+            for (int i = 0; i < D; ++i) cm += mu[i] * nu[d2][i];
+            sj += v[d2][j];
+            dk += v[d2][j] * (cm - A);
+            for (int i = 0; i < D; ++i) dm[i] += v[d2][j] * (nu[d2][i] - cm * mu[i]);
+        }
+        draw[K * D + K + j] = dpg * m.lam[j] * (sj - pg);
+        float kp = raw[K * D + j];
+        if (kp > -8.f && kp < 8.f) draw[K * D + j] = dpg * m.lam[j] * m.kappa[j] * dk;
+        float nn = 0.f;
+        for (int i = 0; i < D; ++i) nn += raw[j * D + i] * raw[j * D + i];
+        if (nn > 0.f) {
+            float inv = rsqrtf(nn);
+            for (int i = 0; i < D; ++i) draw[j * D + i] = dpg * m.lam[j] * m.kappa[j] * dm[i] * inv;
+        }
+    }
+    if (a.c_mode == 0) draw[K * (D + 2)] = -a.e_sel * wt * (pg - pu) / ptil * inv_n * c * (1.f - c);
+    return loss;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const int tid = threadIdx.x, tl = tid >> 7, row = tid & 127;
+    const bool issuer = row == 0;
+    uint8_t *wimg = sm;
+    uint8_t *tb = sm + kWImgBytes + tl * kTileBytes;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kWImgBytes + 2 * kTileBytes);
+    uint32_t *tptr = reinterpret_cast<uint32_t *>(mbar + 2);
+    for (int i = tid; i < kWImgBytes / 16; i += kTrainBlock) reinterpret_cast<uint4 *>(wimg)[i] = __ldg(a.f.wimg + i);
+    if (tid == 0) { mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1); fence_mbar_init(); }
+    if (tid < 32) tmem_alloc(tptr, 512);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tb0 = *tptr + (uint32_t)(tl * 256);
+    TTile t{tb, tb + kTX, tb + kTX + kTH, tb + kTX + 2 * kTH, tb + kTX + 2 * kTH + kTG, wimg, &mbar[tl],
+            tb0, tb0 + 64, tb0 + 128, tb0 + 192, 0u, 1 + tl};
+
+    const long long nrec = (long long)min((unsigned long long)a.rec_cap, *a.rec_ctr);
+    const float inv_n = nrec > 0 ? 1.f / (float)nrec : 0.f;
+    const long long ntiles = (nrec + 127) / 128;
+    const size_t T = (size_t)1 << a.f.log2T;
+    bool have_acc = false, ok = true;
+    float db3 = 0.f;      // column `row` (< kOutPad) of the bias gradient
+    double loss_local = 0.0;
+
+    for (long long tile = (long long)blockIdx.x * 2 + tl; tile < ntiles && ok; tile += (long long)gridDim.x * 2) {
+        const long long ri = tile * 128 + row;
+        const bool valid = ri < nrec;
+        float rec[12];
+        if (valid) {
+            const float4 *p = reinterpret_cast<const float4 *>(a.rec + ri * 12);
+            float4 r0 = __ldg(p), r1 = __ldg(p + 1), r2 = __ldg(p + 2);
+            rec[0] = r0.x; rec[1] = r0.y; rec[2] = r0.z; rec[3] = r0.w;
+            rec[4] = r1.x; rec[5] = r1.y; rec[6] = r1.z; rec[7] = r1.w;
+            rec[8] = r2.x; rec[9] = r2.y; rec[10] = r2.z; rec[11] = r2.w;
+            encode_row<D>(a.f, rec, t.X, row);
+        } else {
+            for (int i = 0; i < 12; ++i) rec[i] = 0.f;
+            for (int c = 0; c < kFeat; c += 8) *reinterpret_cast<uint4 *>(t.X + cm_offset(row, c, kFeat)) = make_uint4(0, 0, 0, 0);
+        }
+        // ---- forward recomputation ----
+        ok = tt_issue_wait(t, issuer, [&] { umma_gemm(t.s0, t.X, 0, kFeat, t.w, 0, kFeat, kHid, kFeat, false); }, a.err);
+        if (!ok) break;
+        float h[kHid];
+        ld_cols(t.s0, row, kHid, h);
+        for (int c = 0; c < kHid; c += 8) {
+            float v8[8];
+            for (int i = 0; i < 8; ++i) v8[i] = fmaxf(h[c + i], 0.f);
+            st_row8_bf16(t.H1, row, c, kHid, v8);
+        }
+        ok = tt_issue_wait(t, issuer, [&] { umma_gemm(t.s0, t.H1, 0, kHid, t.w + kW1Bytes, 0, kHid, kHid, kHid, false); }, a.err);
+        if (!ok) break;
+        ld_cols(t.s0, row, kHid, h);
+        for (int c = 0; c < kHid; c += 8) {
+            float v8[8];
+            for (int i = 0; i < 8; ++i) v8[i] = fmaxf(h[c + i], 0.f);
+            st_row8_bf16(t.H2, row, c, kHid, v8);
+        }
+        ok = tt_issue_wait(t, issuer, [&] { umma_gemm(t.s0, t.H2, 0, kHid, t.w + kW1Bytes + kW2Bytes, 0, kHid, kOutPad, kHid, false); }, a.err);
+        if (!ok) break;
+        float raw[kOutPad];
+        ld_cols(t.s0, row, kOutPad, raw);
+        for (int i = 0; i < kOutPad; ++i) raw[i] += __ldg(a.f.b3 + i);
+        // ---- loss gradient at the raw outputs ----
+        float dy[kOutPad];
+        if (valid) loss_local += record_grad<D>(a, rec, raw, inv_n, dy);
+        else for (int i = 0; i < kOutPad; ++i) dy[i] = 0.f;
+        for (int c = 0; c < kOutPad; c += 8) st_row8_split(t.G, t.Gl, row, c, 128, dy + c);
+        {
+            float z8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            st_row8_bf16(t.G, row, kOutPad, 128, z8);
+            st_row8_bf16(t.G, row, kOutPad + 8, 128, z8);
+            st_row8_bf16(t.Gl, row, kOutPad, 128, z8);
+            st_row8_bf16(t.Gl, row, kOutPad + 8, 128, z8);
+        }
+        // dH2 = dY W3 (W3 image rows = outputs = K here -> MN-major B)
+        ok = tt_issue_wait(t, issuer, [&] {
+            const uint8_t *W3 = t.w + kW1Bytes + kW2Bytes;
+            umma_gemm(t.s0, t.G, 0, 128, W3, 1, kHid, kHid, kOutPad, false);
+            umma_gemm(t.s0, t.Gl, 0, 128, W3, 1, kHid, kHid, kOutPad, true);
+        }, a.err);
+        if (!ok) break;
+        // bias gradient: column sums of the dY tiles (hi + lo, what the MMAs see)
+        if (row < kOutPad) {
+            float s = 0.f;
+            for (int r = 0; r < 128; ++r)
+                s += __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(t.G + cm_offset(r, row, 128))) +
+                     __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(t.Gl + cm_offset(r, row, 128)));
+            db3 += s;
+        }
+        ld_cols(t.s0, row, kHid, h);
+        {
+            float h2[kHid];
+            for (int c = 0; c < kHid; c += 8) ld_row8_bf16(t.H2, row, c, kHid, h2 + c);
+            for (int c = 0; c < kHid; c += 8) {
+                float v8[8];
+                for (int i = 0; i < 8; ++i) v8[i] = h2[c + i] > 0.f ? h[c + i] : 0.f;
+                st_row8_split(t.G, t.Gl, row, 64 + c, 128, v8);
+            }
+        }
+        // dW3 (+)= [dY|dZ2]^T H2 (rows 0..47 used); dH1 = dZ2 W2
+        ok = tt_issue_wait(t, issuer, [&] {
+            umma_gemm(t.acc3, t.G, 1, 128, t.H2, 1, kHid, kHid, 128, have_acc);
+            umma_gemm(t.acc3, t.Gl, 1, 128, t.H2, 1, kHid, kHid, 128, true);
+            umma_gemm(t.s0, t.G + cm_offset(0, 64, 128), 0, 128, t.w + kW1Bytes, 1, kHid, kHid, kHid, false);
+            umma_gemm(t.s0, t.Gl + cm_offset(0, 64, 128), 0, 128, t.w + kW1Bytes, 1, kHid, kHid, kHid, true);
+        }, a.err);
+        if (!ok) break;
+        ld_cols(t.s0, row, kHid, h);
+        {
+            float h1[kHid];
+            for (int c = 0; c < kHid; c += 8) ld_row8_bf16(t.H1, row, c, kHid, h1 + c);
+            for (int c = 0; c < kHid; c += 8) {
+                float v8[8];
+                for (int i = 0; i < 8; ++i) v8[i] = h1[c + i] > 0.f ? h[c + i] : 0.f;
+                st_row8_split(t.G, t.Gl, row, c, 128, v8);
+            }
+        }
+        // dW2 (+)= [dZ1|dZ2]^T H1 (rows 64..127), dW1 (+)= [dZ1|dZ2]^T X (rows 0..63), dX = dZ1 W1
+        ok = tt_issue_wait(t, issuer, [&] {
+            umma_gemm(t.acc2, t.G, 1, 128, t.H1, 1, kHid, kHid, 128, have_acc);
+            umma_gemm(t.acc2, t.Gl, 1, 128, t.H1, 1, kHid, kHid, 128, true);
+            umma_gemm(t.acc1, t.G, 1, 128, t.X, 1, kFeat, kFeat, 128, have_acc);
+            umma_gemm(t.acc1, t.Gl, 1, 128, t.X, 1, kFeat, kFeat, 128, true);
+            umma_gemm(t.s0, t.G, 0, 128, t.w, 1, kFeat, kFeat, kHid, false);
+            umma_gemm(t.s0, t.Gl, 0, 128, t.w, 1, kFeat, kFeat, kHid, true);
+        }, a.err);
+        if (!ok) break;
+        have_acc = true;
+        {
+            float dx[kFeat];
+            ld_cols(t.s0, row, kFeat, dx);   // warp-uniform TMEM load
+            if (valid) {
+                float u[D];
+                unit_coords<D>(a.f, rec, u);
+                for (int l = 0; l < a.f.L; ++l) {
+                    uint32_t idx[1 << D];
+                    float w[1 << D];
+                    level_corners<D>(a.f, l, u, idx, w);
+                    for (int m = 0; m < (1 << D); ++m) {
+                        float *gp = a.g_grid + ((size_t)l * T + idx[m]) * 2;
+                        atomicAdd(reinterpret_cast<float2 *>(gp), make_float2(w[m] * dx[2 * l], w[m] * dx[2 * l + 1]));
+                    }
+                }
+            }
+        }
+    }
+    // flush TMEM accumulators (each warp reads its own 32 lanes)
+    if (have_acc && ok) {
+        // TMEM loads are warp-collective: every lane loads, then stores conditionally
+        float v[kHid];
+        ld_cols(t.acc3, row, kHid, v);
+        if (row < kOutPad) for (int i = 0; i < kHid; ++i) atomicAdd(a.g_W3 + (size_t)row * kHid + i, v[i]);
+        ld_cols(t.acc2, row, kHid, v);
+        if (row >= 64) for (int i = 0; i < kHid; ++i) atomicAdd(a.g_W2 + (size_t)(row - 64) * kHid + i, v[i]);
+        ld_cols(t.acc1, row, kFeat, v);
+        if (row < 64) for (int i = 0; i < kFeat; ++i) atomicAdd(a.g_W1 + (size_t)row * kFeat + i, v[i]);
+        if (row < kOutPad) atomicAdd(a.g_b3 + row, db3);
+    }
+    // loss: warp reduction then one atomic per warp
+    for (int o = 16; o; o >>= 1) loss_local += __shfl_xor_sync(0xffffffffu, loss_local, o);
+    if ((tid & 31) == 0) atomicAdd(a.loss_acc, loss_local);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid < 32) tmem_dealloc(*tptr, 512);
+}
+
+// Adam on a flat FP32 array
+__global__ void adam_kernel(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float gi = g[i];
+    float mi = b1 * m[i] + (1.f - b1) * gi;
+    float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void grid_to_half_kernel(const float *g32, __half2 *g16, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) g16[i] = __floats2half2_rn(g32[2 * i], g32[2 * i + 1]);
+}
+
+// FP32 MLP master (exchange layout) -> BF16 core-matrix weight image + padded bias
+__global__ void weight_image_kernel(const float *mlp, int nout, uint8_t *img, float *b3pad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float *W1 = mlp, *W2 = W1 + kHid * kFeat, *W3 = W2 + kHid * kHid, *b3 = W3 + nout * kHid;
+    __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(img);
+    if (i < kHid * kFeat) {
+        int r = i / kFeat, c = i % kFeat;
+        o[cm_offset(r, c, kFeat) / 2] = __float2bfloat16_rn(W1[i]);
+    }
+    if (i < kHid * kHid) {
+        int r = i / kHid, c = i % kHid;
+        o[(kW1Bytes + cm_offset(r, c, kHid)) / 2] = __float2bfloat16_rn(W2[i]);
+    }
+    if (i < kOutPad * kHid) {
+        int r = i / kHid, c = i % kHid;
+        float val = r < nout ? W3[r * kHid + c] : 0.f;
+        o[(kW1Bytes + kW2Bytes + cm_offset(r, c, kHid)) / 2] = __float2bfloat16_rn(val);
+    }
+    if (i < kOutPad) b3pad[i] = i < nout ? b3[i] : 0.f;
+}
+
+wost_status refresh_inference_copy(wost_field *f, cudaStream_t st) {
+    int64_t ne = (int64_t)f->desc.levels * f->T;
+    grid_to_half_kernel<<<(int)((ne + 255) / 256), 256, 0, st>>>(f->grid32, f->grid16, ne);
+    weight_image_kernel<<<(kHid * kHid + 255) / 256, 256, 0, st>>>(f->mlp32, f->nout, f->wimg, f->b3pad);
+    WOST_CUDA(cudaGetLastError());
+    return WOST_OK;
+}
+
+// gradient of the mean loss over the record buffer into f->grid_g / f->mlp_g
+wost_status train_grad_launch(wost_field *f, int dim, cudaStream_t st) {
+    WOST_CUDA(cudaMemsetAsync(f->grid_g, 0, f->n_grid() * sizeof(float), st));
+    WOST_CUDA(cudaMemsetAsync(f->mlp_g, 0, f->n_mlp() * sizeof(float), st));
+    WOST_CUDA(cudaMemsetAsync(f->loss_acc, 0, sizeof(double), st));
+    TrainArgs a{};
+    a.f = f->dev();
+    a.rec = f->rec;
+    a.rec_ctr = f->rec_ctr;
+    a.rec_cap = f->rec_cap;
+    a.c_mode = f->t_c_mode;
+    a.c_fixed = f->t_c_fixed;
+    a.reflect = f->t_reflect;
+    a.e_sel = f->desc.e_sel;
+    a.g_grid = f->grid_g;
+    a.g_W1 = f->mlp_g;
+    a.g_W2 = a.g_W1 + kHid * kFeat;
+    a.g_W3 = a.g_W2 + kHid * kHid;
+    a.g_b3 = a.g_W3 + (size_t)f->nout * kHid;
+    a.loss_acc = reinterpret_cast<double *>(f->loss_acc);
+    a.err = device_err_flag();
+    // one CTA per SM: each CTA holds all 512 TMEM columns of its SM
+    int grid = num_sms();
+    static bool attr2 = false, attr3 = false;
+    if (dim == 2) {
+        if (!attr2) { WOST_CUDA(cudaFuncSetAttribute(train_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem)); attr2 = true; }
+        train_kernel<2><<<grid, kTrainBlock, kTrainSmem, st>>>(a);
+    } else {
+        if (!attr3) { WOST_CUDA(cudaFuncSetAttribute(train_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem)); attr3 = true; }
+        train_kernel<3><<<grid, kTrainBlock, kTrainSmem, st>>>(a);
+    }
+    WOST_CUDA(cudaGetLastError());
+    return WOST_OK;
+}
+
+wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *) {
+    wost_status rc = train_grad_launch(f, dim, st);
+    if (rc != WOST_OK || !apply_adam) return rc;
+    f->adam_t++;
+    const wost_field_desc &d = f->desc;
+    float c1 = 1.f - powf(d.beta1, (float)f->adam_t), c2 = 1.f - powf(d.beta2, (float)f->adam_t);
+    int64_t ng = f->n_grid(), nm = f->n_mlp();
+    adam_kernel<<<(int)((ng + 255) / 256), 256, 0, st>>>(f->grid32, f->grid_g, f->grid_m, f->grid_v, ng, d.lr_grid,
+                                                         d.beta1, d.beta2, d.adam_eps, c1, c2);
+    adam_kernel<<<(int)((nm + 255) / 256), 256, 0, st>>>(f->mlp32, f->mlp_g, f->mlp_m, f->mlp_v, nm, d.lr_mlp,
+                                                         d.beta1, d.beta2, d.adam_eps, c1, c2);
+    WOST_CUDA(cudaGetLastError());
+    return refresh_inference_copy(f, st);
+}
+
+}  // namespace wost

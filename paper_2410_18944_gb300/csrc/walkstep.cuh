@@ -1,0 +1,183 @@
+// One walk-on-stars step, shared by the plain and the guided persistent
+// kernels (Sec. 3.2 Eq. wost_estm, reparameterised as in Sec. 4.1):
+//   1. closest Dirichlet point; stop inside the epsilon-shell (FP64 re-test)
+//      or at the step cap, adding T g(xbar) to the point's FP64 sums;
+//   2. star radius r = max(min(R_D, R_S), eps) from the closest silhouette;
+//   3. source term -(r^2 / 2d) f(y), y ~ Green-function density, if visible;
+//   4. (caller) direction nu and step weight;
+//   5. first Neumann hit within r (FP64 re-test of the winner) or x + r nu.
+// Random numbers: Philox4x32-10, counter (point, walk, step, purpose).
+#pragma once
+#include "geom.cuh"
+
+namespace wost {
+
+struct WalkArgs {
+    DevScene sc;
+    const double *points;      // npoints * D
+    const uint8_t *status;     // 0 walk, 1 shell, 2 outside
+    int64_t npoints;
+    int walk_begin;
+    unsigned long long total;  // work items = npoints * walks in this launch
+    unsigned long long *work_ctr;
+    double *sum, *sum2;
+    float eps;
+    double eps64;
+    int maxsteps;
+    uint32_t key0, key1;
+    unsigned long long *stat;  // [0] walk-steps, [1] truncated, [2] walks, [3..6] node/Dirichlet/silhouette/Neumann visits
+    int *err;
+};
+
+template <int D>
+struct Walk {
+    float x[D], n[D];
+    float T, acc;
+    uint32_t pid, wid;
+    int k, prim;     // prim: Neumann leaf slot the walker stands on, -1 if interior
+};
+
+template <int D>
+__device__ __forceinline__ void uniform_dir(float u0, float u1, float *v) {
+    if (D == 2) {
+        float s, c;
+        sincospif(2.f * u0, &s, &c);
+        v[0] = c;
+        v[1] = s;
+    } else {
+        float z = 1.f - 2.f * u0, s, c;
+        float st = sqrtf(fmaxf(0.f, 1.f - z * z));
+        sincospif(2.f * u1, &s, &c);
+        v[0] = st * c;
+        v[1] = st * s;
+        v[2] = z;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ float dotv(const float *a, const float *b) {
+    float s = a[0] * b[0] + a[1] * b[1];
+    if (D == 3) s += a[2] * b[2];
+    return s;
+}
+
+template <int D>
+__device__ __forceinline__ void reflect(float *v, const float *n) {
+    float t = 2.f * dotv<D>(v, n);
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] -= t * n[i];
+}
+
+// Beta(2,2) by inversion of F(s) = 3 s^2 - 2 s^3 (trigonometric root)
+__device__ __forceinline__ float beta22_inv(float u) {
+    return 0.5f + cosf((acosf(1.f - 2.f * u) + 4.f * WOST_PI) / 3.f);
+}
+
+template <int D>
+__device__ __forceinline__ void start_walk(Walk<D> &w, const WalkArgs &a, unsigned long long item) {
+    w.pid = (uint32_t)(item % (unsigned long long)a.npoints);
+    w.wid = (uint32_t)(a.walk_begin + item / (unsigned long long)a.npoints);
+#pragma unroll
+    for (int i = 0; i < D; ++i) { w.x[i] = (float)a.points[(size_t)w.pid * D + i]; w.n[i] = 0.f; }
+    w.T = 1.f;
+    w.acc = 0.f;
+    w.k = 0;
+    w.prim = -1;
+}
+
+__device__ __forceinline__ void finish_walk(const WalkArgs &a, uint32_t pid, float value) {
+    atomicAdd(a.sum + pid, (double)value);
+    atomicAdd(a.sum2 + pid, (double)value * (double)value);
+}
+
+// Steps 1-3.  Returns true if the walk ended (its value already added).
+// On return false: r (star radius) and S (this step's source term).
+template <int D>
+__device__ __forceinline__ bool step_geometry(Walk<D> &w, const WalkArgs &a, float &r, float &S,
+                                              float &term_value, bool &truncated, Visits *vis) {
+    const DevScene &sc = a.sc;
+    float bd2;
+    int slot = closest_dirichlet<D>(sc.dir, w.x, bd2, a.err, vis);
+    double q64[3];
+    double dD = dirichlet_dist64<D>(sc.dir, slot, w.x, q64);
+    bool shell = dD <= a.eps64;
+    if (shell || w.k >= a.maxsteps) {
+        float xb[3] = {(float)q64[0], (float)q64[1], D == 3 ? (float)q64[2] : 0.f};
+        term_value = eval_fn<D>(sc.g, xb);
+        w.acc += w.T * term_value;
+        truncated = !shell;
+        return true;
+    }
+    float RD = (float)dD;
+    float bs = RD * RD;
+    closest_silhouette<D>(sc.sil, w.x, sc.tau, bs, a.err, vis, sc.sil_cones);
+    float R = fminf(sqrtf(bs), RD);
+    r = fmaxf(R, a.eps);
+    S = 0.f;
+    if (sc.has_source) {
+        U4 u = philox(w.pid, w.wid, (uint32_t)w.k, P_SRC, a.key0, a.key1);
+        float vs[D];
+        uniform_dir<D>(u01(u.x), u01(u.y), vs);
+        if (w.prim >= 0 && dotv<D>(vs, w.n) < 0.f) reflect<D>(vs, w.n);
+        float rho = D == 2 ? r * sqrtf(u01(u.z) * u01(u.w)) : r * beta22_inv(u01(u.z));
+        float th;
+        int hs = ray_neumann<D>(sc.neu, w.x, vs, rho, w.prim, th, a.err, vis);
+        if (hs >= 0) {
+            double t64;
+            if (!ray_prim64<D>(sc.neu, hs, w.x, vs, t64) || t64 > (double)rho) hs = -1;
+        }
+        if (hs < 0) {
+            float y[3];
+#pragma unroll
+            for (int i = 0; i < D; ++i) y[i] = w.x[i] + rho * vs[i];
+            S = -(r * r / (2.f * D)) * eval_fn<D>(sc.f, y);
+        }
+        w.acc += w.T * S;
+    }
+    return false;
+}
+
+// Step 5: ray cast within r and move.
+template <int D>
+__device__ __forceinline__ void step_move(Walk<D> &w, const WalkArgs &a, const float *nu, float r, Visits *vis) {
+    const DevScene &sc = a.sc;
+    float th;
+    int hit = ray_neumann<D>(sc.neu, w.x, nu, r, w.prim, th, a.err, vis);
+    if (hit >= 0) {
+        double t64;
+        if (!ray_prim64<D>(sc.neu, hit, w.x, nu, t64) || t64 > (double)r) hit = -1;
+    }
+    if (hit >= 0) {
+        float ng[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) { w.x[i] += th * nu[i]; ng[i] = __ldg(sc.nin_neu + (size_t)hit * D + i); }
+        float sg = dotv<D>(ng, nu) < 0.f ? 1.f : -1.f;
+#pragma unroll
+        for (int i = 0; i < D; ++i) w.n[i] = sg * ng[i];
+        w.prim = hit;
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) w.x[i] += r * nu[i];
+        w.prim = -1;
+    }
+    w.k++;
+}
+
+// block-level sum of the per-thread counters into the launch statistics
+__device__ __forceinline__ void flush_counters(const WalkArgs &a, unsigned long long steps, unsigned long long trunc,
+                                               unsigned long long walks, const Visits &v) {
+    __shared__ unsigned long long red[7];
+    if (threadIdx.x < 7) red[threadIdx.x] = 0;
+    __syncthreads();
+    atomicAdd(&red[0], steps);
+    atomicAdd(&red[1], trunc);
+    atomicAdd(&red[2], walks);
+    atomicAdd(&red[3], (unsigned long long)v.nodes);
+    atomicAdd(&red[4], (unsigned long long)v.dprims);
+    atomicAdd(&red[5], (unsigned long long)v.sprims);
+    atomicAdd(&red[6], (unsigned long long)v.nprims);
+    __syncthreads();
+    if (threadIdx.x < 7) atomicAdd(a.stat + threadIdx.x, red[threadIdx.x]);
+}
+
+}  // namespace wost

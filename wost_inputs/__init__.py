@@ -375,13 +375,31 @@ def config_small_laplace():
     return sc, pts
 
 
+def inside_star_polygon(sc: Scene, pts: np.ndarray) -> np.ndarray:
+    """Exact insideness for a polygon whose vertices are sorted by angle
+    around the origin (star-shaped w.r.t. 0): find the edge spanning each
+    point's direction and compare the point with that edge's line."""
+    v = sc.verts
+    ang = np.arctan2(v[:, 1], v[:, 0]) % (2 * np.pi)
+    order = np.argsort(ang)
+    va, aa = v[order], ang[order]
+    th = np.arctan2(pts[:, 1], pts[:, 0]) % (2 * np.pi)
+    j = np.searchsorted(aa, th, side="right")
+    a = va[(j - 1) % len(va)]
+    b = va[j % len(va)]
+    # inside iff p is on the origin's side of the line a-b
+    cross_p = (b[:, 0] - a[:, 0]) * (pts[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (pts[:, 0] - a[:, 0])
+    cross_o = (b[:, 0] - a[:, 0]) * (0 - a[:, 1]) - (b[:, 1] - a[:, 1]) * (0 - a[:, 0])
+    return np.sign(cross_p) == np.sign(cross_o)
+
+
 def config_star_guided(res: int = 512, nseg: int = 4096, seed: int = 2):
     """4096-segment seeded star polyline, 40% zero-flux Neumann arc, Dirichlet
     x^2 - y^2; res x res grid over the bounding box masked to the interior."""
     sc = star_polyline(nseg, seed)
     lo, hi = sc.bbox
     pts = grid_points_2d(res, lo, hi)
-    pts = pts[inside_polygon_mask_chunked(sc, pts)]
+    pts = pts[inside_star_polygon(sc, pts)]
     return sc, pts
 
 
