@@ -331,8 +331,36 @@ def run_ours(args):
     return 0
 
 
+def run_once(args):
+    """One solve of (a seeded subset of) the workload, for profilers: no
+    timing loop, no oracle.  --once plain|guided, --points N, --spp S."""
+    import torch
+    import wost_inputs as wi
+    from paper_2410_18944_gb300 import api, build
+    build.build()
+    sc, pts = make_workload()
+    if args.points and args.points < len(pts):
+        pts = wi.subsample(pts, args.points, seed=1)
+    S = api.Scene(sc)
+    lo, hi = S.bbox()
+    F = api.Field(2, lo, hi)
+    p = torch.tensor(pts, dtype=torch.float64, device="cuda")
+    guided = args.once == "guided"
+    for rep in range(2):
+        m, v, st = api.solve(S, p, args.spp, eps=WORKLOAD["eps"], maxsteps=WORKLOAD["maxsteps"], seed=rep,
+                             guided=guided, field=F if guided else None, train=1 if guided else 0)
+        torch.cuda.synchronize()
+        print(json.dumps({"once": args.once, "rep": rep, **{k: st[k] for k in (
+            "walk_steps", "ms_walk", "ms_train", "node_visits", "prim_visits", "kernel_launches", "records")}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--once", choices=["plain", "guided"], default=None,
+                    help="run one solve of the workload (profiling), no timing")
+    ap.add_argument("--points", type=int, default=0, help="with --once: seeded subset of the query points")
+    ap.add_argument("--spp", type=int, default=WORKLOAD["spp"], help="with --once: walks per point")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -345,6 +373,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.once:
+        return run_once(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -147,17 +147,38 @@ __device__ __forceinline__ void load_tri(const float4 *__restrict__ P, int s, fl
     a[0] = u.x; a[1] = u.y; a[2] = u.z; b[0] = u.w; b[1] = v.x; b[2] = v.y; c[0] = v.z; c[1] = v.w; c[2] = w.x;
 }
 
+// ---- warp-synchronous traversal ------------------------------------------------
+// Every traversal below runs as a loop whose iterations are taken together by
+// all lanes of the warp that entered it (a warp vote at the loop head): in one
+// iteration each unfinished lane processes one inner node or one leaf, then
+// pops its stack if needed.  Lanes that diverge inside an iteration
+// re-converge at its end, instead of drifting apart for the rest of the
+// traversal.
+#define WOST_POP(stack, sd, sp, ref, done, best)               \
+    do {                                                       \
+        bool found_ = false;                                   \
+        while (sp > 0) {                                       \
+            --sp;                                              \
+            if (sd[sp] <= best) { ref = stack[sp]; found_ = true; break; } \
+        }                                                      \
+        if (!found_) done = true;                              \
+    } while (0)
+
 // ---- closest Dirichlet primitive -------------------------------------------
 // returns the leaf slot of the closest primitive (-1 if none); best = squared distance
 template <int D>
 __device__ int closest_dirichlet(const DevBVH &bv, const float *x, float &best, int *err, Visits *vis = nullptr) {
     best = __int_as_float(0x7f800000);
     if (bv.nprims == 0) return -1;
+    const unsigned mask = __activemask();
     int best_slot = -1, best_id = 0x7fffffff;
     int stack[kStack];
     float sd[kStack];
     int sp = 0, ref = 0;
-    for (;;) {
+    bool done = false;
+    while (__any_sync(mask, !done)) {
+        if (done) continue;
+        bool pop = false;
         if (ref >= 0) {
             float d0, d1;
             int r0, r1;
@@ -169,9 +190,13 @@ __device__ int closest_dirichlet(const DevBVH &bv, const float *x, float &best, 
                 if (sp < kStack) { stack[sp] = first0 ? r1 : r0; sd[sp] = first0 ? d1 : d0; ++sp; }
                 else atomicOr(err, 1);
                 ref = first0 ? r0 : r1;
-                continue;
-            } else if (h0) { ref = r0; continue; }
-            else if (h1) { ref = r1; continue; }
+            } else if (h0) {
+                ref = r0;
+            } else if (h1) {
+                ref = r1;
+            } else {
+                pop = true;
+            }
         } else {
             int s0 = leaf_start(ref), cnt = leaf_count(ref);
             if (vis) vis->dprims += cnt;
@@ -191,13 +216,9 @@ __device__ int closest_dirichlet(const DevBVH &bv, const float *x, float &best, 
                     if (d2 < best || id < best_id) { best = d2; best_slot = s; best_id = id; }
                 }
             }
+            pop = true;
         }
-        bool found = false;
-        while (sp > 0) {
-            --sp;
-            if (sd[sp] <= best) { ref = stack[sp]; found = true; break; }
-        }
-        if (!found) break;
+        if (pop) WOST_POP(stack, sd, sp, ref, done, best);
     }
     return best_slot;
 }
@@ -275,11 +296,15 @@ template <int D>
 __device__ int closest_silhouette(const DevBVH &bv, const float *x, float tau, float &best, int *err,
                                    Visits *vis = nullptr, const float4 *cones = nullptr) {
     if (bv.nprims == 0) return -1;
+    const unsigned mask = __activemask();
     int best_slot = -1, best_id = 0x7fffffff;
     int stack[kStack];
     float sd[kStack];
     int sp = 0, ref = 0;
-    for (;;) {
+    bool done = false;
+    while (__any_sync(mask, !done)) {
+        if (done) continue;
+        bool pop = false;
         if (ref >= 0) {
             float d0, d1;
             int r0, r1;
@@ -297,9 +322,13 @@ __device__ int closest_silhouette(const DevBVH &bv, const float *x, float tau, f
                 if (sp < kStack) { stack[sp] = first0 ? r1 : r0; sd[sp] = first0 ? d1 : d0; ++sp; }
                 else atomicOr(err, 1);
                 ref = first0 ? r0 : r1;
-                continue;
-            } else if (h0) { ref = r0; continue; }
-            else if (h1) { ref = r1; continue; }
+            } else if (h0) {
+                ref = r0;
+            } else if (h1) {
+                ref = r1;
+            } else {
+                pop = true;
+            }
         } else {
             int s0 = leaf_start(ref), cnt = leaf_count(ref);
             if (vis) vis->sprims += cnt;
@@ -310,7 +339,6 @@ __device__ int closest_silhouette(const DevBVH &bv, const float *x, float tau, f
                     float4 e0 = __ldg(bv.prims + 2 * s), e1 = __ldg(bv.prims + 2 * s + 1);
                     float rx = x[0] - e0.x, ry = x[1] - e0.y;
                     d2 = rx * rx + ry * ry;
-                    if (d2 > best) continue;
                     o0 = e0.z * rx + e0.w * ry;
                     o1 = e1.x * rx + e1.y * ry;
                     always = e1.z != 0.f;
@@ -319,23 +347,19 @@ __device__ int closest_silhouette(const DevBVH &bv, const float *x, float tau, f
                     float4 e2 = __ldg(bv.prims + 4 * s + 2), e3 = __ldg(bv.prims + 4 * s + 3);
                     float a[3] = {e0.x, e0.y, e0.z}, b[3] = {e0.w, e1.x, e1.y};
                     d2 = seg3_d2<float>(a, b, x);
-                    if (d2 > best) continue;
                     float r[3] = {x[0] - a[0], x[1] - a[1], x[2] - a[2]};
                     o0 = e1.z * r[0] + e1.w * r[1] + e2.x * r[2];
                     o1 = e2.y * r[0] + e2.z * r[1] + e2.w * r[2];
                     always = e3.x != 0.f;
                 }
-                if (!(always || sil_rule(o0, o1, tau))) continue;
-                int id = __ldg(bv.ids + s);
-                if (d2 < best || id < best_id) { best = d2; best_slot = s; best_id = id; }
+                if (d2 <= best && (always || sil_rule(o0, o1, tau))) {
+                    int id = __ldg(bv.ids + s);
+                    if (d2 < best || id < best_id) { best = d2; best_slot = s; best_id = id; }
+                }
             }
+            pop = true;
         }
-        bool found = false;
-        while (sp > 0) {
-            --sp;
-            if (sd[sp] <= best) { ref = stack[sp]; found = true; break; }
-        }
-        if (!found) break;
+        if (pop) WOST_POP(stack, sd, sp, ref, done, best);
     }
     return best_slot;
 }
@@ -412,7 +436,9 @@ __device__ __forceinline__ bool ray_prim64(const DevBVH &bv, int s, const float 
 template <int D>
 __device__ int ray_neumann(const DevBVH &bv, const float *o, const float *v, float tmax, int skip, float &thit,
                            int *err, Visits *vis = nullptr) {
+    thit = tmax;
     if (bv.nprims == 0) return -1;
+    const unsigned mask = __activemask();
     float inv[3];
 #pragma unroll
     for (int k = 0; k < D; ++k) inv[k] = 1.f / v[k];   // +-inf for a zero component is fine in the slab test
@@ -421,7 +447,10 @@ __device__ int ray_neumann(const DevBVH &bv, const float *o, const float *v, flo
     int stack[kStack];
     float st[kStack];
     int sp = 0, ref = 0;
-    for (;;) {
+    bool done = false;
+    while (__any_sync(mask, !done)) {
+        if (done) continue;
+        bool pop = false;
         if (ref >= 0) {
             float t0, t1;
             int r0, r1;
@@ -433,27 +462,26 @@ __device__ int ray_neumann(const DevBVH &bv, const float *o, const float *v, flo
                 if (sp < kStack) { stack[sp] = first0 ? r1 : r0; st[sp] = first0 ? t1 : t0; ++sp; }
                 else atomicOr(err, 1);
                 ref = first0 ? r0 : r1;
-                continue;
-            } else if (h0) { ref = r0; continue; }
-            else if (h1) { ref = r1; continue; }
+            } else if (h0) {
+                ref = r0;
+            } else if (h1) {
+                ref = r1;
+            } else {
+                pop = true;
+            }
         } else {
             int s0 = leaf_start(ref), cnt = leaf_count(ref);
             if (vis) vis->nprims += cnt;
             for (int s = s0; s < s0 + cnt; ++s) {
-                if (s == skip) continue;
                 float t;
-                if (ray_prim<D>(bv.prims, s, o, v, t) && t <= best) {
+                if (s != skip && ray_prim<D>(bv.prims, s, o, v, t) && t <= best) {
                     int id = __ldg(bv.ids + s);
                     if (t < best || id < best_id) { best = t; best_slot = s; best_id = id; }
                 }
             }
+            pop = true;
         }
-        bool found = false;
-        while (sp > 0) {
-            --sp;
-            if (st[sp] <= best) { ref = stack[sp]; found = true; break; }
-        }
-        if (!found) break;
+        if (pop) WOST_POP(stack, st, sp, ref, done, best);
     }
     thit = best;
     return best_slot;
@@ -463,12 +491,16 @@ __device__ int ray_neumann(const DevBVH &bv, const float *o, const float *v, flo
 template <int D>
 __device__ int ray_count(const DevBVH &bv, const float *o, const float *v, int *err) {
     if (bv.nprims == 0) return 0;
+    const unsigned mask = __activemask();
     float inv[3];
 #pragma unroll
     for (int k = 0; k < D; ++k) inv[k] = 1.f / v[k];
     const float big = 3.0e38f;
     int cnt = 0, stack[kStack], sp = 0, ref = 0;
-    for (;;) {
+    bool done = false;
+    while (__any_sync(mask, !done)) {
+        if (done) continue;
+        bool pop = false;
         if (ref >= 0) {
             float t0, t1;
             int r0, r1;
@@ -477,18 +509,25 @@ __device__ int ray_count(const DevBVH &bv, const float *o, const float *v, int *
             if (h0 && h1) {
                 if (sp < kStack) stack[sp++] = r1; else atomicOr(err, 1);
                 ref = r0;
-                continue;
-            } else if (h0) { ref = r0; continue; }
-            else if (h1) { ref = r1; continue; }
+            } else if (h0) {
+                ref = r0;
+            } else if (h1) {
+                ref = r1;
+            } else {
+                pop = true;
+            }
         } else {
             int s0 = leaf_start(ref), c = leaf_count(ref);
             for (int s = s0; s < s0 + c; ++s) {
                 float t;
                 cnt += ray_prim<D>(bv.prims, s, o, v, t) ? 1 : 0;
             }
+            pop = true;
         }
-        if (sp == 0) break;
-        ref = stack[--sp];
+        if (pop) {
+            if (sp == 0) done = true;
+            else ref = stack[--sp];
+        }
     }
     return cnt;
 }
