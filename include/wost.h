@@ -223,6 +223,32 @@ wost_status wost_mixture_sample(int32_t dim, int32_t K, const float *mu, const f
                                 const float *lambda, const uint32_t *counters, uint64_t seed,
                                 uint32_t scene_id, int64_t n, float *out_nu, float *out_pdf);
 
+/* ---- plain solve without device allocation ---------------------------------- */
+/* The paper has no counterpart to this entry point; it exists for callers
+   that cannot allocate device memory while solving -- for instance when
+   another component owns the whole device memory pool, or in a loop that
+   must not pay the device-wide synchronisation implied by cudaFree.
+   wost_solve_plain_static runs the plain (unguided) walk of wost_solve, with
+   the same random streams, but keeps all of its scratch memory (per-point
+   FP64 sums, point status, work counter, statistics) in one fixed array
+   compiled into the library (about 6.6 MB, present on every GPU that loads
+   the library until the process exits).  It calls no cudaMalloc / cudaFree.
+     points_dev    device, npoints * dim doubles (caller-owned)
+     out_mean_dev  device, npoints doubles (caller-owned); out_var_dev
+                   nullable, variance of the mean
+     npoints       at most WOST_STATIC_MAX_POINTS, else WOST_ERR_INVALID_ARG
+     stream        cudaStream_t (NULL = default); synchronised before return
+     out_walk_steps (nullable, host) walk-steps of the solve
+   The first call on a device looks up the array's device address with
+   cudaGetSymbolAddress (make it before any stream capture).  Every call
+   reuses the same array and clears what must start at zero; calls whose GPU
+   work overlaps (e.g. issued on two streams) race on it. */
+#define WOST_STATIC_MAX_POINTS 262144
+wost_status wost_solve_plain_static(wost_scene *scene, const double *points_dev, int64_t npoints,
+                                    int32_t nwalks, double eps, int32_t maxsteps, uint64_t seed,
+                                    void *stream, double *out_mean_dev, double *out_var_dev,
+                                    int64_t *out_walk_steps);
+
 /* ---- diagnostics ---------------------------------------------------------- */
 /* D[128 x N] = A[128 x K] B[N x K]^T (host float arrays, row-major) through
    the library's tensor-core path (BF16 operands, FP32 accumulation); a_mn /

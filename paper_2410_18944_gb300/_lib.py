@@ -91,6 +91,8 @@ SIGNATURES = {
     "wost_mixture_sample": (C.c_int, [C.c_int32, C.c_int32, _fp, _fp, _fp, _u32p, C.c_uint64, C.c_uint32,
                                       C.c_int64, _fp, _fp]),
     "wost_diag_umma": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _fp, _fp, _fp]),
+    "wost_solve_plain_static": (C.c_int, [_vp, _vp, C.c_int64, C.c_int32, C.c_double, C.c_int32, C.c_uint64, _vp,
+                                          _vp, _vp, _i64p]),
 }
 
 
