@@ -34,10 +34,16 @@ def _deps():
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     os.makedirs(OUT, exist_ok=True)
     newest = max(os.path.getmtime(f) for f in _deps())
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
+    stamp = os.path.join(OUT, "flags.txt")
+    want = " ".join(os.environ.get("WOST_NVCC_FLAGS", "").split())
+    have = open(stamp).read() if os.path.exists(stamp) else ""
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest and have == want:
         return LIB
     nvcc = _nvcc()
-    flags = FLAGS + list(extra_flags or [])
+    # WOST_NVCC_FLAGS: extra compile flags for tuning experiments (e.g.
+    # "-DWOST_BVH_LEAF=8"); part of the dependency check via the stamp file
+    env_flags = os.environ.get("WOST_NVCC_FLAGS", "").split()
+    flags = FLAGS + list(extra_flags or []) + env_flags
 
     def compile_one(src):
         obj = os.path.join(OUT, src.replace(".cu", ".o"))
@@ -57,6 +63,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(stamp, "w") as fh:
+        fh.write(want)
     return LIB
 
 

@@ -14,6 +14,10 @@
 #include "common.cuh"
 #include "umma.cuh"
 
+#ifndef WOST_GRID_L2_ONLY
+#define WOST_GRID_L2_ONLY 1
+#endif
+
 namespace wost {
 
 constexpr int kFeat = 32;     // L * F
@@ -102,7 +106,14 @@ __device__ __forceinline__ void encode_row(const DevField &f, const float *x, ui
             float a0 = 0.f, a1 = 0.f;
 #pragma unroll
             for (int m = 0; m < (1 << D); ++m) {
-                float2 g = __half22float2(__ldg(f.grid16 + (size_t)l * T + idx[m]));
+#if WOST_GRID_L2_ONLY
+                // the table is gathered at random: keep it out of L1 (which
+                // holds the BVH) and serve it from L2
+                __half2 hv = __ldcg(f.grid16 + (size_t)l * T + idx[m]);
+#else
+                __half2 hv = __ldg(f.grid16 + (size_t)l * T + idx[m]);
+#endif
+                float2 g = __half22float2(hv);
                 a0 = fmaf(w[m], g.x, a0);
                 a1 = fmaf(w[m], g.y, a1);
             }

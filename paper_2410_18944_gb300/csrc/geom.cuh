@@ -176,10 +176,12 @@ __device__ int closest_dirichlet(const DevBVH &bv, const float *x, float &best, 
     float sd[kStack];
     int sp = 0, ref = 0;
     bool done = false;
+    // while-while: descend inner nodes together until every lane holds a
+    // leaf (or is done), then test the leaves together
     while (__any_sync(mask, !done)) {
-        if (done) continue;
-        bool pop = false;
-        if (ref >= 0) {
+        while (__any_sync(mask, !done && ref >= 0)) {
+            if (done || ref < 0) continue;
+            bool pop = false;
             float d0, d1;
             int r0, r1;
             node_box_d2<D>(bv.nodes, ref, x, d0, d1, r0, r1);
@@ -197,7 +199,9 @@ __device__ int closest_dirichlet(const DevBVH &bv, const float *x, float &best, 
             } else {
                 pop = true;
             }
-        } else {
+            if (pop) WOST_POP(stack, sd, sp, ref, done, best);
+        }
+        if (!done && ref < 0) {
             int s0 = leaf_start(ref), cnt = leaf_count(ref);
             if (vis) vis->dprims += cnt;
             for (int s = s0; s < s0 + cnt; ++s) {
@@ -216,9 +220,8 @@ __device__ int closest_dirichlet(const DevBVH &bv, const float *x, float &best, 
                     if (d2 < best || id < best_id) { best = d2; best_slot = s; best_id = id; }
                 }
             }
-            pop = true;
+            WOST_POP(stack, sd, sp, ref, done, best);
         }
-        if (pop) WOST_POP(stack, sd, sp, ref, done, best);
     }
     return best_slot;
 }
@@ -302,10 +305,12 @@ __device__ int closest_silhouette(const DevBVH &bv, const float *x, float tau, f
     float sd[kStack];
     int sp = 0, ref = 0;
     bool done = false;
+    // while-while: descend inner nodes together until every lane holds a
+    // leaf (or is done), then test the leaves together
     while (__any_sync(mask, !done)) {
-        if (done) continue;
-        bool pop = false;
-        if (ref >= 0) {
+        while (__any_sync(mask, !done && ref >= 0)) {
+            if (done || ref < 0) continue;
+            bool pop = false;
             float d0, d1;
             int r0, r1;
             node_box_d2<D>(bv.nodes, ref, x, d0, d1, r0, r1);
@@ -329,7 +334,9 @@ __device__ int closest_silhouette(const DevBVH &bv, const float *x, float tau, f
             } else {
                 pop = true;
             }
-        } else {
+            if (pop) WOST_POP(stack, sd, sp, ref, done, best);
+        }
+        if (!done && ref < 0) {
             int s0 = leaf_start(ref), cnt = leaf_count(ref);
             if (vis) vis->sprims += cnt;
             for (int s = s0; s < s0 + cnt; ++s) {
@@ -357,9 +364,8 @@ __device__ int closest_silhouette(const DevBVH &bv, const float *x, float tau, f
                     if (d2 < best || id < best_id) { best = d2; best_slot = s; best_id = id; }
                 }
             }
-            pop = true;
+            WOST_POP(stack, sd, sp, ref, done, best);
         }
-        if (pop) WOST_POP(stack, sd, sp, ref, done, best);
     }
     return best_slot;
 }
@@ -448,10 +454,12 @@ __device__ int ray_neumann(const DevBVH &bv, const float *o, const float *v, flo
     float st[kStack];
     int sp = 0, ref = 0;
     bool done = false;
+    // while-while: descend inner nodes together until every lane holds a
+    // leaf (or is done), then test the leaves together
     while (__any_sync(mask, !done)) {
-        if (done) continue;
-        bool pop = false;
-        if (ref >= 0) {
+        while (__any_sync(mask, !done && ref >= 0)) {
+            if (done || ref < 0) continue;
+            bool pop = false;
             float t0, t1;
             int r0, r1;
             node_box_ray<D>(bv.nodes, ref, o, inv, best, t0, t1, r0, r1);
@@ -469,7 +477,9 @@ __device__ int ray_neumann(const DevBVH &bv, const float *o, const float *v, flo
             } else {
                 pop = true;
             }
-        } else {
+            if (pop) WOST_POP(stack, st, sp, ref, done, best);
+        }
+        if (!done && ref < 0) {
             int s0 = leaf_start(ref), cnt = leaf_count(ref);
             if (vis) vis->nprims += cnt;
             for (int s = s0; s < s0 + cnt; ++s) {
@@ -479,9 +489,8 @@ __device__ int ray_neumann(const DevBVH &bv, const float *o, const float *v, flo
                     if (t < best || id < best_id) { best = t; best_slot = s; best_id = id; }
                 }
             }
-            pop = true;
+            WOST_POP(stack, st, sp, ref, done, best);
         }
-        if (pop) WOST_POP(stack, st, sp, ref, done, best);
     }
     thit = best;
     return best_slot;

@@ -106,97 +106,286 @@ __device__ __forceinline__ void end_recorded_walk(const GuidedArgs &g, int slot,
     }
 }
 
+// ===========================================================================
+// Warp-specialised guided walk.  One CTA per SM:
+//   warps 0-3  (server): issue the three tcgen05 MMAs of a decode tile and run
+//              the TMEM epilogues (warp q owns TMEM lanes 32q..32q+31);
+//   warps 4-19 (walkers): one walk per thread; per step each walker warp runs
+//              its geometry, claims a 32-row quarter of a decode tile, writes
+//              its features, and waits only for that tile.
+// Tiles are formed from whichever walker warps are ready (quarters are claimed
+// in order from a shared counter), through rings of mbarriers over kNT tile
+// buffers: full (4 quarter arrivals), done (one per quarter), empty (4
+// consumer arrivals).  When a tile stays partly claimed the server closes it
+// (compare-and-swap on the claim counter) and zero-pads the missing quarters,
+// so a few remaining walkers never wait for partners that will not come.
+// Every wait is bounded; a give-up sets the error word and ends the loops.
+// ===========================================================================
+constexpr int kWsServerWarps = 4;
+#ifndef WOST_WS_WALKERS
+#define WOST_WS_WALKERS 12
+#endif
+#ifndef WOST_WS_TILES
+#define WOST_WS_TILES 2
+#endif
+constexpr int kWsWalkerWarps = WOST_WS_WALKERS;
+constexpr int kWsThreads = 32 * (kWsServerWarps + kWsWalkerWarps);
+constexpr int kNT = WOST_WS_TILES;           // decode tile buffers (few: leaves L1 for the BVH)
+constexpr uint32_t kWsTmemCols = tmem_cols(kNT * 64);   // allocation rounded up to a power of two
+static_assert(kNT >= 1 && kNT * 64 <= 512, "decode tile buffers must fit in the 512 TMEM columns");
+constexpr int kYStride = 49;                 // fp32 output row stride (conflict-free)
+constexpr int kYBytes = 128 * kYStride * 4;
+constexpr int kBufBytes = kXTileBytes + kHTileBytes + kYBytes;
+constexpr int kWsCtrlBytes = 512;
+constexpr int kWsSmem = kWImgBytes + kNT * kBufBytes + kWsCtrlBytes;
+constexpr uint32_t kFlushPolls = 256;        // server polls before closing a partial tile
+constexpr uint32_t kWaitLimit = 1u << 22;    // bound of every wait loop
+
+struct WsCtrl {
+    uint64_t full[kNT], done[kNT][4], empty[kNT], mma;
+    int qclaim, alive, go, padmask;
+    uint32_t tmem;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" : : "r"(smem_u32(bar)) : "memory");
+}
+
+// all lanes of the calling warp poll; returns false on give-up
+__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 template <int D>
-__global__ void __launch_bounds__(kGuidedBlock, 2) guided_walk_kernel(GuidedArgs g) {
+__global__ void __launch_bounds__(kWsThreads, 1) guided_walk_kernel(GuidedArgs g) {
     extern __shared__ __align__(1024) uint8_t sm[];
     const WalkArgs &a = g.w;
-    CtaTiles ct = cta_tiles_setup(sm, g.f);
-    const int tid = threadIdx.x, tile = tid >> 7, row = tid & 127;
-    const bool issuer = row == 0;
-    TileCtx t{ct.xt + tile * kXTileBytes, ct.ht + tile * kHTileBytes, ct.wimg, &ct.mbar[tile],
-              *ct.tptr + (uint32_t)(tile * 64), 0u, 1 + tile};
-    const int slot = blockIdx.x * kGuidedBlock + tid;
-    const float area = D == 2 ? 2.f * WOST_PI : 4.f * WOST_PI;
+    uint8_t *wimg = sm;
+    uint8_t *bufs = sm + kWImgBytes;
+    WsCtrl *ctl = reinterpret_cast<WsCtrl *>(sm + kWImgBytes + kNT * kBufBytes);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    auto Xb = [&](int b) { return bufs + b * kBufBytes; };
+    auto Hb = [&](int b) { return bufs + b * kBufBytes + kXTileBytes; };
+    auto Yb = [&](int b) { return reinterpret_cast<float *>(bufs + b * kBufBytes + kXTileBytes + kHTileBytes); };
 
-    Walk<D> w;
+    for (int i = tid; i < kWImgBytes / 16; i += kWsThreads) reinterpret_cast<uint4 *>(wimg)[i] = __ldg(g.f.wimg + i);
+    if (tid == 0) {
+        for (int b = 0; b < kNT; ++b) {
+            mbar_init(&ctl->full[b], 4);
+            mbar_init(&ctl->empty[b], 4);
+            for (int q = 0; q < 4; ++q) mbar_init(&ctl->done[b][q], 1);
+        }
+        mbar_init(&ctl->mma, 1);
+        ctl->qclaim = 0;
+        ctl->alive = kWsWalkerWarps;
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&ctl->tmem, kWsTmemCols);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem0 = ctl->tmem;
+
     Visits vis;
-    bool active = false, exhausted = false;
     unsigned long long nsteps = 0, ntrunc = 0, nwalks = 0;
-    for (;;) {
-        // one fetch attempt per iteration; no lane leaves or skips ahead, so the
-        // tile stays in step and re-converges at every named barrier
-        if (!active && !exhausted) {
-            unsigned long long item = warp_fetch_add(a.work_ctr, true);
-            if (item >= a.total) {
-                exhausted = true;
-            } else {
-                start_walk<D>(w, a, item);
-                if (a.status[w.pid] == 0) { active = true; nwalks++; }
+
+    if (warp < kWsServerWarps) {
+        // ------------------------------ server ------------------------------
+        uint32_t mma_phase = 0;
+        const int row = tid;   // TMEM lane of this thread (warp q owns 32q..32q+31)
+        for (int T = 0;; ++T) {
+            const int b = T % kNT;
+            const uint32_t k = (uint32_t)(T / kNT);
+            if (tid == 0) {
+                int go = -1, pad = 0;
+                uint32_t polls = 0;
+                for (uint32_t it = 0; it < kWaitLimit; ++it) {
+                    if (mbar_try_wait(&ctl->full[b], k & 1u)) { go = 1; break; }
+                    if (++polls < kFlushPolls) continue;
+                    polls = 0;
+                    int q = *(volatile int *)&ctl->qclaim;
+                    if (q <= 4 * T) {
+                        if (*(volatile int *)&ctl->alive == 0) { go = 0; break; }
+                    } else if (q < 4 * T + 4 && atomicCAS(&ctl->qclaim, q, 4 * T + 4) == q) {
+                        // close the tile: zero-fill the unclaimed quarters and arrive for them
+                        for (int qq = q - 4 * T; qq < 4; ++qq) {
+                            pad |= 1 << qq;
+                            for (int r = 32 * qq; r < 32 * qq + 32; ++r)
+                                for (int c = 0; c < kFeat; c += 8)
+                                    *reinterpret_cast<uint4 *>(Xb(b) + cm_offset(r, c, kFeat)) = make_uint4(0, 0, 0, 0);
+                        }
+                        fence_async_smem();
+                        for (int qq = q - 4 * T; qq < 4; ++qq) mbar_arrive(&ctl->full[b]);
+                    }
+                }
+                if (go < 0) atomicOr(a.err, 2);
+                ctl->go = go;
+                ctl->padmask = pad;
             }
-        }
-        if (!named_or(1 + tile, 128, active || !exhausted)) break;
-        bool live = active;
-        float r = 0.f, S = 0.f;
-        if (live) {
-            nsteps++;
-            float gv;
-            bool trunc = false;
-            if (step_geometry<D>(w, a, r, S, gv, trunc, &vis)) {
-                finish_walk(a, w.pid, w.acc);
-                if (g.record) end_recorded_walk<D>(g, slot, w.k, gv);
-                ntrunc += trunc;
-                active = live = false;
-            }
-        }
-        if (live) encode_row<D>(g.f, w.x, t.xtile, row);
-        else zero_row(t.xtile, row, kFeat);
-        float raw[kOutPad];
-        if (!mlp_tile_forward(t, g.f, row, issuer, raw, a.err)) break;
-        if (live) {
-            Mixture<D> m;
-            theta_map<D, 8>(raw, m);
-            const float c = g.c_mode ? g.c_fixed : m.c;
-            float nu[D];
-            bool from_guide = sample_direction<D, 8>(m, c, w.pid, w.wid, (uint32_t)w.k, a.key0, a.key1, nu);
-            const bool onN = w.prim >= 0;
-            bool zero_density = false;
-            if (onN) {
-                float dn = dotv<D>(nu, w.n);
-                if (dn < 0.f && (g.reflect || !from_guide)) { reflect<D>(nu, w.n); dn = -dn; }
-                zero_density = dn <= 0.f;   // Eq. angular_req: the recursive term is 0
-            }
-            if (zero_density) {
-                finish_walk(a, w.pid, w.acc);
-                if (g.record) end_recorded_walk<D>(g, slot, w.k, S);
-                active = false;
-            } else {
-                float pg = mixture_pdf<D, 8>(m, nu);
-                if (onN && g.reflect) {
-                    float nm[D];
+            named_sync(1, 128);
+            const int go = ctl->go, pad = ctl->padmask;
+            named_sync(1, 128);
+            if (go <= 0) break;
+            const uint32_t tm = tmem0 + (uint32_t)(b * 64);
+            bool ok = true;
+            // three layers: X -> H -> H -> Y (TMEM columns [b*64, b*64 + 64))
+            for (int layer = 0; layer < 3 && ok; ++layer) {
+                if (tid == 0) {
+                    tc_fence_after();
+                    if (layer == 0) umma_gemm(tm, Xb(b), 0, kFeat, wimg, 0, kFeat, kHid, kFeat, false);
+                    else if (layer == 1) umma_gemm(tm, Hb(b), 0, kHid, wimg + kW1Bytes, 0, kHid, kHid, kHid, false);
+                    else umma_gemm(tm, Hb(b), 0, kHid, wimg + kW1Bytes + kW2Bytes, 0, kHid, kOutPad, kHid, false);
+                    umma_commit(&ctl->mma);
+                }
+                ok = mbar_wait_bounded(&ctl->mma, mma_phase, kWaitLimit);
+                mma_phase ^= 1u;
+                tc_fence_after();
+                ok = !named_or(1, 128, !ok);
+                if (!ok) break;
+                if (layer < 2) {
+                    for (int c = 0; c < kHid; c += 16) {
+                        float v[16];
+                        tmem_ld16(lane_addr(tm, row, c), v);
+                        tmem_ld_wait();
 #pragma unroll
-                    for (int i = 0; i < D; ++i) nm[i] = nu[i];
-                    reflect<D>(nm, w.n);
-                    pg += mixture_pdf<D, 8>(m, nm);
+                        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+                        st_row8_bf16(Hb(b), row, c, kHid, v);
+                        st_row8_bf16(Hb(b), row, c + 8, kHid, v + 8);
+                    }
+                    fence_async_smem();
+                    tc_fence_before();
+                    named_sync(1, 128);
+                } else {
+                    float *y = Yb(b) + row * kYStride;
+                    for (int c = 0; c < kOutPad; c += 16) {
+                        float v[16];
+                        tmem_ld16(lane_addr(tm, row, c), v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) y[c + i] = v[i] + __ldg(g.f.b3 + c + i);
+                    }
+                    tc_fence_before();
                 }
-                const float alpha = onN ? 0.5f : 1.f;
-                const float pu = (onN ? 2.f : 1.f) / area;
-                const float ptil = c * pg + (1.f - c) * pu;
-                // |S| alpha p_u == 1 exactly, so c = 0 gives weight 1 as in plain WoSt
-                const float wgt = 1.f / (c * area * alpha * pg + (1.f - c));
-                if (g.record) {
-                    float4 *rr = reinterpret_cast<float4 *>(g.scratch + ((size_t)slot * a.maxsteps + w.k) * kRecFloats);
-                    float n2 = onN && D == 3 ? w.n[D - 1] : 0.f;
-                    rr[0] = make_float4(w.x[0], w.x[1], D == 3 ? w.x[2] : 0.f, nu[0]);
-                    rr[1] = make_float4(nu[1], D == 3 ? nu[2] : 0.f, onN ? w.n[0] : 0.f, onN ? w.n[1] : 0.f);
-                    rr[2] = make_float4(n2, ptil, wgt, S);
-                }
-                w.T *= wgt;
-                step_move<D>(w, a, nu, r, &vis);
+            }
+            if (!ok) {
+                if (tid == 0) atomicOr(a.err, 2);
+                break;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&ctl->done[b][warp]);
+                if (pad & (1 << warp)) mbar_arrive(&ctl->empty[b]);   // no consumer for a padded quarter
             }
         }
+    } else {
+        // ------------------------------ walkers -----------------------------
+        const int slot = blockIdx.x * (kWsWalkerWarps * 32) + (tid - 32 * kWsServerWarps);
+        const float area = D == 2 ? 2.f * WOST_PI : 4.f * WOST_PI;
+        Walk<D> w;
+        bool active = false, exhausted = false, failed = false;
+        for (;;) {
+            if (!active && !exhausted) {
+                unsigned long long item = warp_fetch_add(a.work_ctr, true);
+                if (item >= a.total) {
+                    exhausted = true;
+                } else {
+                    start_walk<D>(w, a, item);
+                    if (a.status[w.pid] == 0) { active = true; nwalks++; }
+                }
+            }
+            if (!__any_sync(0xffffffffu, active || !exhausted)) break;
+            __syncwarp();
+            float r = 0.f, S = 0.f;
+            if (active) {
+                nsteps++;
+                float gv;
+                bool trunc = false;
+                if (step_geometry<D>(w, a, r, S, gv, trunc, &vis)) {
+                    finish_walk(a, w.pid, w.acc);
+                    if (g.record) end_recorded_walk<D>(g, slot, w.k, gv);
+                    ntrunc += trunc;
+                    active = false;
+                }
+            }
+            const bool live = active;
+            if (!__any_sync(0xffffffffu, live)) continue;
+            // claim a quarter of a decode tile
+            int qi = 0;
+            if (lane == 0) qi = atomicAdd(&ctl->qclaim, 1);
+            qi = __shfl_sync(0xffffffffu, qi, 0);
+            const int T = qi >> 2, quarter = qi & 3, b = T % kNT;
+            const uint32_t k = (uint32_t)(T / kNT);
+            if (T >= kNT && !ws_wait(&ctl->empty[b], (k - 1u) & 1u)) { failed = true; break; }
+            const int row = 32 * quarter + lane;
+            if (live) encode_row<D>(g.f, w.x, Xb(b), row);
+            else zero_row(Xb(b), row, kFeat);
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->full[b]);
+            if (!ws_wait(&ctl->done[b][quarter], k & 1u)) { failed = true; break; }
+            float nu[D];
+            bool zero_density = false;
+            float wgt = 1.f, ptil = 0.f;
+            if (live) {
+                RowMixture<D, 8> m;
+                m.init(Yb(b) + row * kYStride);
+                const float c = g.c_mode ? g.c_fixed : m.c();
+                bool from_guide = sample_direction_row<D, 8>(m, c, w.pid, w.wid, (uint32_t)w.k, a.key0, a.key1, nu);
+                const bool onN = w.prim >= 0;
+                if (onN) {
+                    float dn = dotv<D>(nu, w.n);
+                    if (dn < 0.f && (g.reflect || !from_guide)) { reflect<D>(nu, w.n); dn = -dn; }
+                    zero_density = dn <= 0.f;   // Eq. angular_req: the recursive term is 0
+                }
+                if (!zero_density) {
+                    float nm[D];
+                    const bool refl = onN && g.reflect;
+                    if (refl) {
+#pragma unroll
+                        for (int i = 0; i < D; ++i) nm[i] = nu[i];
+                        reflect<D>(nm, w.n);
+                    }
+                    const float pg = m.pdf(nu, refl ? nm : nullptr);
+                    const float alpha = onN ? 0.5f : 1.f;
+                    const float pu = (onN ? 2.f : 1.f) / area;
+                    ptil = c * pg + (1.f - c) * pu;
+                    // |S| alpha p_u == 1 exactly, so c = 0 gives weight 1 as in plain WoSt
+                    wgt = 1.f / (c * area * alpha * pg + (1.f - c));
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->empty[b]);   // tile rows consumed
+            if (live) {
+                if (zero_density) {
+                    finish_walk(a, w.pid, w.acc);
+                    if (g.record) end_recorded_walk<D>(g, slot, w.k, S);
+                    active = false;
+                } else {
+                    if (g.record) {
+                        const bool onN = w.prim >= 0;
+                        float4 *rr = reinterpret_cast<float4 *>(g.scratch + ((size_t)slot * a.maxsteps + w.k) * kRecFloats);
+                        float n2 = onN && D == 3 ? w.n[D - 1] : 0.f;
+                        rr[0] = make_float4(w.x[0], w.x[1], D == 3 ? w.x[2] : 0.f, nu[0]);
+                        rr[1] = make_float4(nu[1], D == 3 ? nu[2] : 0.f, onN ? w.n[0] : 0.f, onN ? w.n[1] : 0.f);
+                        rr[2] = make_float4(n2, ptil, wgt, S);
+                    }
+                    w.T *= wgt;
+                    step_move<D>(w, a, nu, r, &vis);
+                }
+            }
+        }
+        if (failed) atomicOr(a.err, 2);
+        __syncwarp();
+        if (lane == 0) atomicSub(&ctl->alive, 1);
     }
     flush_counters(a, nsteps, ntrunc, nwalks, vis);
-    cta_tiles_teardown(ct);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem0, kWsTmemCols);
 }
 
 // decode of arbitrary points: the same tile forward as inside the walk
@@ -268,28 +457,21 @@ wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_ada
 
 int guided_ctas_per_sm() { return 1; }
 
-// resident CTAs per SM of the guided kernel (each holds 128 TMEM columns,
-// so at most 4 may share an SM)
+// the warp-specialised walk kernel runs one CTA (640 threads) per SM
 wost_status guided_occupancy(int dim, int *per_sm) {
-    static int occ[4] = {0, 0, 0, 0};
-    if (!occ[dim]) {
-        int n = 0;
-        if (dim == 2) {
-            WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGuidedSmem));
-            WOST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, guided_walk_kernel<2>, kGuidedBlock, kGuidedSmem));
-        } else {
-            WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGuidedSmem));
-            WOST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, guided_walk_kernel<3>, kGuidedBlock, kGuidedSmem));
-        }
-        occ[dim] = std::max(1, std::min(n, 4));
+    static bool set[4] = {false, false, false, false};
+    if (!set[dim]) {
+        if (dim == 2) WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmem));
+        else WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmem));
+        set[dim] = true;
     }
-    *per_sm = occ[dim];
+    *per_sm = 1;
     return WOST_OK;
 }
 
 wost_status launch_guided(int dim, const GuidedArgs &g, int grid, cudaStream_t st) {
-    if (dim == 2) guided_walk_kernel<2><<<grid, kGuidedBlock, kGuidedSmem, st>>>(g);
-    else guided_walk_kernel<3><<<grid, kGuidedBlock, kGuidedSmem, st>>>(g);
+    if (dim == 2) guided_walk_kernel<2><<<grid, kWsThreads, kWsSmem, st>>>(g);
+    else guided_walk_kernel<3><<<grid, kWsThreads, kWsSmem, st>>>(g);
     WOST_CUDA(cudaGetLastError());
     return WOST_OK;
 }
@@ -315,7 +497,7 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
     const bool any_train = ex.train && walk_begin < ex.train_until_wpp;
     if (any_train) {
         int64_t cap = ex.max_train_records > 0 ? ex.max_train_records : std::max<int64_t>(a.npoints * 64, 1 << 20);
-        size_t scratch = (size_t)grid * kGuidedBlock * (size_t)std::max(a.maxsteps, 1) * kRecFloats * sizeof(float);
+        size_t scratch = (size_t)grid * (kWsWalkerWarps * 32) * (size_t)std::max(a.maxsteps, 1) * kRecFloats * sizeof(float);
         wost_status rc = ensure_records(f, cap, scratch);
         if (rc != WOST_OK) return rc;
     }

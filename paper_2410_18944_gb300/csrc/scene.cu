@@ -15,7 +15,10 @@ namespace wost {
 
 namespace {
 
-constexpr int kLeaf = 4;
+#ifndef WOST_BVH_LEAF
+#define WOST_BVH_LEAF 16
+#endif
+constexpr int kLeaf = WOST_BVH_LEAF;   // primitives per leaf (<= 16)
 constexpr int kBins = 16;
 constexpr int kSahDepth = 40;   // beyond this depth, median splits bound the tree depth
 

@@ -63,6 +63,13 @@ __device__ __forceinline__ void umma_commit(uint64_t *mbar) {
                  : "memory");
 }
 
+// tcgen05.alloc takes a power-of-two column count in [32, 512]
+__host__ __device__ constexpr uint32_t tmem_cols(uint32_t n) {
+    uint32_t c = 32;
+    while (c < n) c <<= 1;
+    return c;
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  :

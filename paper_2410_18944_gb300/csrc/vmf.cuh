@@ -208,3 +208,98 @@ __device__ __forceinline__ bool sample_direction(const Mixture<D> &m, float c, u
 }
 
 }  // namespace wost
+
+namespace wost {
+
+// ---------------------------------------------------------------------------
+// The same direction draw and densities, reading the raw network outputs of
+// one walk from a shared-memory row (stride-49 float rows) lobe by lobe
+// instead of holding the whole mixture in registers.
+// ---------------------------------------------------------------------------
+template <int D, int K>
+struct RowMixture {
+    const float *y;     // raw outputs: mu' (K x D), kappa' (K), lambda' (K), c'
+    float lam[K];       // normalised mixture weights
+
+    __device__ __forceinline__ void init(const float *row) {
+        y = row;
+        float mx = y[K * D + K];
+#pragma unroll
+        for (int i = 1; i < K; ++i) mx = fmaxf(mx, y[K * D + K + i]);
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) { lam[i] = __expf(y[K * D + K + i] - mx); s += lam[i]; }
+        float inv = 1.f / s;
+#pragma unroll
+        for (int i = 0; i < K; ++i) lam[i] *= inv;
+    }
+    __device__ __forceinline__ float c() const { return 1.f / (1.f + __expf(-y[K * (D + 2)])); }
+    __device__ __forceinline__ float kappa(int i) const { return __expf(fminf(fmaxf(y[K * D + i], -8.f), 8.f)); }
+    __device__ __forceinline__ void mu(int i, float *m) const {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) { m[k] = y[i * D + k]; s += m[k] * m[k]; }
+        float inv = s > 0.f ? rsqrtf(s) : 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) m[k] = s > 0.f ? m[k] * inv : (k == 0 ? 1.f : 0.f);
+    }
+    // density of the mixture at nu (and, if nm != nullptr, plus at nm)
+    __device__ __forceinline__ float pdf(const float *nu, const float *nm) const {
+        float p = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            float m[D];
+            mu(i, m);
+            float k = kappa(i), ln = vmf_lognorm<D>(k);
+            float v = __expf(ln - k * half_dist2<D>(m, nu));
+            if (nm) v += __expf(ln - k * half_dist2<D>(m, nm));
+            p += lam[i] * v;
+        }
+        return p;
+    }
+};
+
+template <int D, int K>
+__device__ __forceinline__ bool sample_direction_row(const RowMixture<D, K> &m, float c, uint32_t pid, uint32_t wid,
+                                                     uint32_t step, uint32_t k0, uint32_t k1, float *nu) {
+    U4 u = philox(pid, wid, step, P_MIS, k0, k1);
+    if (u01(u.x) < c) {
+        // first lobe whose running CDF exceeds u1
+        float u1 = u01(u.y), cdf = 0.f;
+        int lobe = K - 1;
+        for (int i = 0; i < K; ++i) {
+            cdf += m.lam[i];
+            if (u1 < cdf) { lobe = i; break; }
+        }
+        float mu[D];
+        m.mu(lobe, mu);
+        float k = m.kappa(lobe);
+        if (D == 2) {
+            float th = vmf2_angle(k, pid, wid, step, k0, k1);
+            float s, cth;
+            sincosf(th, &s, &cth);
+            nu[0] = mu[0] * cth - mu[1] * s;
+            nu[1] = mu[0] * s + mu[1] * cth;
+        } else {
+            vmf3_sample(k, mu, u01(u.z), u01(u.w), nu);
+        }
+        return true;
+    }
+    U4 v = philox(pid, wid, step, P_DIR, k0, k1);
+    if (D == 2) {
+        float s, cth;
+        sincospif(2.f * u01(v.x), &s, &cth);
+        nu[0] = cth;
+        nu[1] = s;
+    } else {
+        float z = 1.f - 2.f * u01(v.x), s, cth;
+        float st = sqrtf(fmaxf(0.f, 1.f - z * z));
+        sincospif(2.f * u01(v.y), &s, &cth);
+        nu[0] = st * cth;
+        nu[1] = st * s;
+        nu[2] = z;
+    }
+    return false;
+}
+
+}  // namespace wost

@@ -12,6 +12,11 @@
 
 namespace wost {
 
+// width of the band (relative to the scene scale) inside which an FP32
+// distance or hit parameter may be on the wrong side of its threshold:
+// 16 units of 2^-24
+constexpr float kRoundBand = 16.f * 5.9604645e-8f;
+
 struct WalkArgs {
     DevScene sc;
     const double *points;      // npoints * D
@@ -98,17 +103,25 @@ __device__ __forceinline__ bool step_geometry(Walk<D> &w, const WalkArgs &a, flo
     const DevScene &sc = a.sc;
     float bd2;
     int slot = closest_dirichlet<D>(sc.dir, w.x, bd2, a.err, vis);
+    float RD = sqrtf(bd2);
+    // eps-shell decision: in FP64 when the FP32 distance lies within its
+    // rounding band around eps (elsewhere both precisions agree)
     double q64[3];
-    double dD = dirichlet_dist64<D>(sc.dir, slot, w.x, q64);
-    bool shell = dD <= a.eps64;
+    bool have64 = false, shell;
+    if (fabsf(RD - a.eps) <= kRoundBand * (sc.scale + RD)) {
+        shell = dirichlet_dist64<D>(sc.dir, slot, w.x, q64) <= a.eps64;
+        have64 = true;
+    } else {
+        shell = RD <= a.eps;
+    }
     if (shell || w.k >= a.maxsteps) {
+        if (!have64) dirichlet_dist64<D>(sc.dir, slot, w.x, q64);
         float xb[3] = {(float)q64[0], (float)q64[1], D == 3 ? (float)q64[2] : 0.f};
         term_value = eval_fn<D>(sc.g, xb);
         w.acc += w.T * term_value;
         truncated = !shell;
         return true;
     }
-    float RD = (float)dD;
     float bs = RD * RD;
     closest_silhouette<D>(sc.sil, w.x, sc.tau, bs, a.err, vis, sc.sil_cones);
     float R = fminf(sqrtf(bs), RD);
@@ -122,7 +135,7 @@ __device__ __forceinline__ bool step_geometry(Walk<D> &w, const WalkArgs &a, flo
         float rho = D == 2 ? r * sqrtf(u01(u.z) * u01(u.w)) : r * beta22_inv(u01(u.z));
         float th;
         int hs = ray_neumann<D>(sc.neu, w.x, vs, rho, w.prim, th, a.err, vis);
-        if (hs >= 0) {
+        if (hs >= 0 && rho - th <= kRoundBand * (sc.scale + rho)) {
             double t64;
             if (!ray_prim64<D>(sc.neu, hs, w.x, vs, t64) || t64 > (double)rho) hs = -1;
         }
@@ -143,7 +156,9 @@ __device__ __forceinline__ void step_move(Walk<D> &w, const WalkArgs &a, const f
     const DevScene &sc = a.sc;
     float th;
     int hit = ray_neumann<D>(sc.neu, w.x, nu, r, w.prim, th, a.err, vis);
-    if (hit >= 0) {
+    // hit-or-reach-r decision: in FP64 when the FP32 hit lies within its
+    // rounding band below r
+    if (hit >= 0 && r - th <= kRoundBand * (sc.scale + r)) {
         double t64;
         if (!ray_prim64<D>(sc.neu, hit, w.x, nu, t64) || t64 > (double)r) hit = -1;
     }
