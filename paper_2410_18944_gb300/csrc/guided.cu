@@ -133,9 +133,16 @@ constexpr int kWsThreads = 32 * (kWsServerWarps + kWsWalkerWarps);
 constexpr int kNT = WOST_WS_TILES;           // decode tile buffers (few: leaves L1 for the BVH)
 constexpr uint32_t kWsTmemCols = tmem_cols(kNT * 64);   // allocation rounded up to a power of two
 static_assert(kNT >= 1 && kNT * 64 <= 512, "decode tile buffers must fit in the 512 TMEM columns");
-constexpr int kYStride = 49;                 // fp32 output row stride (conflict-free)
-constexpr int kYBytes = 128 * kYStride * 4;
-constexpr int kBufBytes = kXTileBytes + kHTileBytes + kYBytes;
+// mbarrier parity waits only tell phase k from k+1: the tiles a buffer can
+// be asked for must never run two generations ahead of its consumption.  The
+// outstanding claims (one per walker warp) span at most floor((W + 2) / 4)
+// tiles beyond the oldest one, and a claim in tile T waits for tile T - kNT.
+static_assert((kWsWalkerWarps + 2) / 4 <= 2 * kNT - 1,
+              "too many walker warps for the decode tile ring (parity waits would alias)");
+constexpr int kYStride = 50;                 // FP16 output row stride (25 words: conflict-free)
+constexpr int kYBytes = 128 * kYStride * 2;  // aliases the hidden tile once layer 3 has run
+static_assert(kYBytes <= kHTileBytes, "decoded outputs must fit in the hidden-activation tile");
+constexpr int kBufBytes = kXTileBytes + kHTileBytes;
 constexpr int kWsCtrlBytes = 512;
 constexpr int kWsSmem = kWImgBytes + kNT * kBufBytes + kWsCtrlBytes;
 constexpr uint32_t kFlushPolls = 256;        // server polls before closing a partial tile
@@ -168,7 +175,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) guided_walk_kernel(GuidedArgs g
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     auto Xb = [&](int b) { return bufs + b * kBufBytes; };
     auto Hb = [&](int b) { return bufs + b * kBufBytes + kXTileBytes; };
-    auto Yb = [&](int b) { return reinterpret_cast<float *>(bufs + b * kBufBytes + kXTileBytes + kHTileBytes); };
+    // decoded raw outputs (FP16) overwrite the hidden tile after the last MMA read it
+    auto Yb = [&](int b) { return reinterpret_cast<__half *>(bufs + b * kBufBytes + kXTileBytes); };
 
     for (int i = tid; i < kWImgBytes / 16; i += kWsThreads) reinterpret_cast<uint4 *>(wimg)[i] = __ldg(g.f.wimg + i);
     if (tid == 0) {
@@ -259,13 +267,17 @@ __global__ void __launch_bounds__(kWsThreads, 1) guided_walk_kernel(GuidedArgs g
                     tc_fence_before();
                     named_sync(1, 128);
                 } else {
-                    float *y = Yb(b) + row * kYStride;
+                    // the layer-3 MMA has completed: its H operand is dead, so
+                    // the FP16 outputs can take its place
+                    __half *y = Yb(b) + row * kYStride;
                     for (int c = 0; c < kOutPad; c += 16) {
                         float v[16];
                         tmem_ld16(lane_addr(tm, row, c), v);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) y[c + i] = v[i] + __ldg(g.f.b3 + c + i);
+                        for (int i = 0; i < 16; i += 2)
+                            *reinterpret_cast<__half2 *>(y + c + i) =
+                                __floats2half2_rn(v[i] + __ldg(g.f.b3 + c + i), v[i + 1] + __ldg(g.f.b3 + c + i + 1));
                     }
                     tc_fence_before();
                 }

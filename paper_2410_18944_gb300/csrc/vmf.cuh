@@ -213,32 +213,34 @@ namespace wost {
 
 // ---------------------------------------------------------------------------
 // The same direction draw and densities, reading the raw network outputs of
-// one walk from a shared-memory row (stride-49 float rows) lobe by lobe
-// instead of holding the whole mixture in registers.
+// one walk (FP16, a shared-memory row) lobe by lobe instead of holding the
+// whole mixture in registers.  Sampling and density use the same values, so
+// the FP16 rounding of the outputs changes the sampler, not its consistency.
 // ---------------------------------------------------------------------------
 template <int D, int K>
 struct RowMixture {
-    const float *y;     // raw outputs: mu' (K x D), kappa' (K), lambda' (K), c'
+    const __half *y;    // raw outputs (FP16): mu' (K x D), kappa' (K), lambda' (K), c'
     float lam[K];       // normalised mixture weights
 
-    __device__ __forceinline__ void init(const float *row) {
+    __device__ __forceinline__ float at(int i) const { return __half2float(y[i]); }
+    __device__ __forceinline__ void init(const __half *row) {
         y = row;
-        float mx = y[K * D + K];
+        float mx = at(K * D + K);
 #pragma unroll
-        for (int i = 1; i < K; ++i) mx = fmaxf(mx, y[K * D + K + i]);
+        for (int i = 1; i < K; ++i) mx = fmaxf(mx, at(K * D + K + i));
         float s = 0.f;
 #pragma unroll
-        for (int i = 0; i < K; ++i) { lam[i] = __expf(y[K * D + K + i] - mx); s += lam[i]; }
+        for (int i = 0; i < K; ++i) { lam[i] = __expf(at(K * D + K + i) - mx); s += lam[i]; }
         float inv = 1.f / s;
 #pragma unroll
         for (int i = 0; i < K; ++i) lam[i] *= inv;
     }
-    __device__ __forceinline__ float c() const { return 1.f / (1.f + __expf(-y[K * (D + 2)])); }
-    __device__ __forceinline__ float kappa(int i) const { return __expf(fminf(fmaxf(y[K * D + i], -8.f), 8.f)); }
+    __device__ __forceinline__ float c() const { return 1.f / (1.f + __expf(-at(K * (D + 2)))); }
+    __device__ __forceinline__ float kappa(int i) const { return __expf(fminf(fmaxf(at(K * D + i), -8.f), 8.f)); }
     __device__ __forceinline__ void mu(int i, float *m) const {
         float s = 0.f;
 #pragma unroll
-        for (int k = 0; k < D; ++k) { m[k] = y[i * D + k]; s += m[k] * m[k]; }
+        for (int k = 0; k < D; ++k) { m[k] = at(i * D + k); s += m[k] * m[k]; }
         float inv = s > 0.f ? rsqrtf(s) : 0.f;
 #pragma unroll
         for (int k = 0; k < D; ++k) m[k] = s > 0.f ? m[k] * inv : (k == 0 ? 1.f : 0.f);
@@ -246,7 +248,7 @@ struct RowMixture {
     // density of the mixture at nu (and, if nm != nullptr, plus at nm)
     __device__ __forceinline__ float pdf(const float *nu, const float *nm) const {
         float p = 0.f;
-#pragma unroll
+#pragma unroll 1
         for (int i = 0; i < K; ++i) {
             float m[D];
             mu(i, m);
