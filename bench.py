@@ -112,6 +112,23 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def combine_ranks(total_ms, steps_local, device=None):
+    """Whole-job figures over all ranks: the slowest rank's timed span (MAX)
+    and the walk-steps of all ranks (SUM).  Single process: unchanged."""
+    try:
+        import torch
+        import torch.distributed as dist
+    except ImportError:
+        return float(total_ms), float(steps_local)
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_ms), float(steps_local)
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(steps_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(n[0])
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -232,7 +249,10 @@ def run_ours(args):
         m, v, st = api.solve(S, pts, WORKLOAD["spp"], seed=1000 * rank + i, **kw)
         if timed_events is not None:
             timed_events[1].record(stream)
+        last_mean[0] = m
         return st
+
+    last_mean = [None]
 
     for i in range(args.warmup):
         one_step(i)
@@ -247,17 +267,8 @@ def run_ours(args):
             per_ms.append(ev[0].elapsed_time(ev[1]))
             stats.append(st)
     barrier()
-    total_ms = sum(per_ms)
     steps_local = sum(s["walk_steps"] for s in stats)
-    t = torch.tensor([total_ms, float(steps_local)], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, steps_all = float(tmax[0]), float(t[1])
-    else:
-        steps_all = float(steps_local)
+    total_ms, steps_all = combine_ranks(sum(per_ms), steps_local, dev)
     value = steps_all / (total_ms / 1000.0)
 
     # end to end through the C ABI with host buffers (pinned points and
@@ -290,6 +301,28 @@ def run_ours(args):
     ev[1].record(stream)
     torch.cuda.synchronize()
     plain_rate = stp["walk_steps"] / (ev[0].elapsed_time(ev[1]) / 1000.0)
+
+    # equal-time relMSE (guided with training vs plain), against a plain
+    # reference at 16x the walks per point; relMSE = mean (u^ - u)^2 / (u^2 + 1e-2)
+    relmse = None
+    if not args.no_relmse:
+        guided_mean = last_mean[0].cpu().numpy()
+        spp_ref = 16 * WORKLOAD["spp"]
+        ref, _, _ = api.solve(S, pts, spp_ref, seed=424242, eps=WORKLOAD["eps"], maxsteps=WORKLOAD["maxsteps"],
+                              stream=stream)
+        ref = ref.cpu().numpy()
+
+        def rel(u):
+            return float(np.mean((u - ref) ** 2 / (ref ** 2 + 1e-2)))
+        t32 = stp["walk_steps"] / plain_rate          # seconds for 32 plain walks per point
+        guided_s = total_ms / args.steps / 1000.0
+        spp_eq = max(1, int(WORKLOAD["spp"] * guided_s / t32))
+        mp_eq, _, _ = api.solve(S, pts, spp_eq, seed=515151, eps=WORKLOAD["eps"], maxsteps=WORKLOAD["maxsteps"],
+                                stream=stream)
+        r_g, r_pe, r_ps = rel(guided_mean), rel(mp_eq.cpu().numpy()), rel(mp.cpu().numpy())
+        relmse = {"guided": r_g, "plain_equal_time": r_pe, "plain_equal_spp": r_ps, "plain_spp_at_equal_time": spp_eq,
+                  "equal_time_ratio_plain_over_guided": r_pe / r_g, "reference": f"plain WoSt, {spp_ref} walks/point",
+                  "guided_s_per_solve": guided_s}
 
     # roofline of the dominant kernel (the guided walk kernel): algorithmic
     # bytes per launch over its average launch time (library CUDA events on
@@ -326,7 +359,8 @@ def run_ours(args):
             "breakdown": {"walk_ms_per_step": walk_ms / len(stats), "train_ms_per_step": train_ms / len(stats),
                           "walk_steps_per_step": steps_local / len(stats),
                           "records_per_step": sum(s["records"] for s in stats) / len(stats)},
-            "plain_walk_steps_per_s": plain_rate}
+            "plain_walk_steps_per_s": plain_rate,
+            "relmse": relmse}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -368,6 +402,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-relmse", action="store_true", help="skip the equal-time relMSE measurement")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the guided walk kernel from an ncu capture")
     args = ap.parse_args()
