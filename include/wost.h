@@ -223,6 +223,69 @@ wost_status wost_mixture_sample(int32_t dim, int32_t K, const float *mu, const f
                                 const float *lambda, const uint32_t *counters, uint64_t seed,
                                 uint32_t scene_id, int64_t n, float *out_nu, float *out_pdf);
 
+/* ---- many scenes in one launch ---------------------------------------------- */
+/* A batch solves many independent problems -- scenes of uneven size, point
+   sets of uneven size, different walk counts, eps, step caps and seeds --
+   with the walks of all of them in one persistent walk launch (per training
+   round when guided fields train, Sec. 5.2), the whole solve captured once
+   into a CUDA graph and replayed by wost_batch_run.  Each job walks exactly
+   as wost_solve(job.scene, job.field, job.points, ...) with exec.seed =
+   job.seed would: the same estimator (Sec. 3.2, Sec. 4) and the same
+   random streams, so a batch differs from the separate solves only in the
+   order of floating-point atomic sums (and, when fields train, in the
+   training steps that follow from that order). */
+typedef struct {
+    wost_scene *scene;
+    wost_field *field;         /* guided batches: this job's field (distinct per job when
+                                  training); NULL in plain batches */
+    const double *points;      /* device, npoints * dim doubles (caller-owned, read at every run) */
+    int64_t npoints;
+    int32_t nwalks;
+    double eps;
+    int32_t maxsteps;
+    uint64_t seed;             /* walk seed (key = seed, scene_id as in wost_solve) */
+    double *out_mean;          /* device, npoints doubles (caller-owned, written at every run) */
+    double *out_var;           /* device, npoints doubles, nullable: variance of the mean */
+} wost_job;
+
+typedef struct wost_batch wost_batch;
+
+/* Launch parameters of a plan and how they were chosen. */
+typedef struct {
+    int32_t ctas_per_sm;       /* plain walk launch: resident CTAs per SM */
+    int32_t flush_polls;       /* guided walk launch: server polls before a partial decode
+                                  tile is closed and zero-padded */
+    int32_t candidates;        /* launch shapes timed by the autotuner (0: none, fixed by exec) */
+    double best_ms, worst_ms;  /* calibration-launch times of the best / worst candidate */
+    int32_t walk_launches;     /* walk launches in the graph (1, or 1 per training round + 1) */
+    int32_t train_steps;       /* training steps in the graph */
+    int64_t graph_nodes;
+} wost_batch_info;
+
+/* Plans a batch of njobs jobs, all of the same dimension: validates them,
+   allocates the batch's work buffers (and the fields' training-record
+   buffers when exec->train), picks the launch parameters and captures the
+   solve into a CUDA graph.  Launch parameters: exec->ctas_per_sm > 0 fixes
+   the plain launch shape; 0 lets an autotuner time candidate shapes (plain:
+   CTAs per SM; guided: the decode-tile flush threshold) on one calibration
+   walk per point of every job and keep the fastest.  Calibration launches
+   record nothing and do not touch the fields.  guided != 0 needs a field
+   per job; exec->c_mode, c_fixed, reflect, train, train_until_wpp and
+   max_train_records apply to every job.  Pointers of the jobs are kept by
+   the plan and must stay valid until wost_batch_destroy. */
+wost_status wost_batch_create(int32_t njobs, const wost_job *jobs, int32_t guided, const wost_exec *exec,
+                              wost_batch **out);
+/* Replays the plan on stream (cudaStream_t, NULL = default stream) and
+   waits for it.  stats (nullable) sums all jobs; ms_walk is the device time
+   of the whole graph (walks and training).  Re-running a plan with training
+   continues to train the fields. */
+wost_status wost_batch_run(wost_batch *batch, void *stream, wost_stats *stats);
+wost_status wost_batch_info_get(const wost_batch *batch, wost_batch_info *info);
+wost_status wost_batch_destroy(wost_batch *batch);
+/* create + run + destroy */
+wost_status wost_solve_batch(int32_t njobs, const wost_job *jobs, int32_t guided, const wost_exec *exec,
+                             wost_stats *stats);
+
 /* ---- plain solve without device allocation ---------------------------------- */
 /* The paper has no counterpart to this entry point; it exists for callers
    that cannot allocate device memory while solving -- for instance when

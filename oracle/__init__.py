@@ -84,6 +84,7 @@ def _declare(L):
     L.orc_closest_dirichlet.argtypes = [C.c_void_p, _dp, _dp, _dp]
     L.orc_closest_silhouette.argtypes = [C.c_void_p, _dp, _dp]
     L.orc_ray_neumann.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_int, _dp]
+    L.orc_ray_neumann_exit.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_int, _dp]
     L.orc_winding.restype = C.c_double
     L.orc_winding.argtypes = [C.c_void_p, _dp]
     L.orc_inward_normal.argtypes = [C.c_void_p, C.c_int, _dp]
@@ -200,7 +201,9 @@ class Scene:
             dist[i] = d.value
         return idx, dist
 
-    def ray_neumann(self, org, dirs, tmax, skip=None):
+    def ray_neumann(self, org, dirs, tmax, skip=None, exit_only=False):
+        """First Neumann hit per ray (all hits, or with exit_only the first
+        primitive the ray leaves the domain through, as the walks cast)."""
         org, dirs = _f64(org), _f64(dirs)
         n = len(org)
         tmax = np.broadcast_to(np.asarray(tmax, float), (n,))
@@ -208,9 +211,9 @@ class Scene:
         idx = np.zeros(n, np.int32)
         t = np.zeros(n)
         tt = C.c_double()
+        fn = lib().orc_ray_neumann_exit if exit_only else lib().orc_ray_neumann
         for i in range(n):
-            idx[i] = lib().orc_ray_neumann(self._h, _d(org[i]), _d(dirs[i]), float(tmax[i]), int(skip[i]),
-                                           C.byref(tt))
+            idx[i] = fn(self._h, _d(org[i]), _d(dirs[i]), float(tmax[i]), int(skip[i]), C.byref(tt))
             t[i] = tt.value
         return idx, t
 

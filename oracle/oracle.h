@@ -53,6 +53,16 @@ int orc_closest_silhouette(const orc_scene *s, const double *x, double *dist);
 /* first Neumann primitive hit by x + t v, 0 < t <= tmax, skipping `skip`. */
 int orc_ray_neumann(const orc_scene *s, const double *x, const double *v, double tmax, int skip,
                     double *t);
+/* the same, counting only primitives the ray leaves the domain through
+   (v . inward normal < 0), whose line / plane it crosses at t > -band within
+   distance band of the primitive, band = 16 * 2^-24 * scale (a walk
+   standing within rounding of a vertex that heads out through the next
+   primitive crosses it at t ~ 0; the walk moves by max(t, 0)).  The walks cast these:
+   inside a closed boundary the first crossing is an exit, and the normal of
+   the walker's new position is then the primitive's inward normal -- the
+   side the walk is on (Sec. 4.1, normal convention at Eq. angular_req). */
+int orc_ray_neumann_exit(const orc_scene *s, const double *x, const double *v, double tmax, int skip,
+                         double *t);
 /* winding number (2D) / generalised winding number (3D) */
 double orc_winding(const orc_scene *s, const double *x);
 /* inward unit normal of a primitive */

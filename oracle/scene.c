@@ -153,8 +153,8 @@ static double prim_closest(const orc_scene *s, int i, const double *x, double *q
     return tri_closest(vert(s, p[0]), vert(s, p[1]), vert(s, p[2]), x, q);
 }
 
-/* ray x + t v against segment a-b (2D): t > 0 and the segment parameter in [0,1] */
-static int ray_seg(const double *x, const double *v, const double *a, const double *b, double *t)
+/* ray x + t v against segment a-b (2D): t > tmin and the segment parameter in [0,1] */
+static int ray_seg(const double *x, const double *v, const double *a, const double *b, double tmin, double *t)
 {
     double e[2] = {b[0] - a[0], b[1] - a[1]};
     double ax[2] = {a[0] - x[0], a[1] - x[1]};
@@ -162,14 +162,14 @@ static int ray_seg(const double *x, const double *v, const double *a, const doub
     if (den == 0) return 0;
     double tt = (ax[0] * e[1] - ax[1] * e[0]) / den;
     double ss = (ax[0] * v[1] - ax[1] * v[0]) / den;
-    if (ss < 0 || ss > 1 || !(tt > 0)) return 0;
+    if (ss < 0 || ss > 1 || !(tt > tmin)) return 0;
     *t = tt;
     return 1;
 }
 
 /* ray against triangle (3D), Moeller & Trumbore (1997) */
 static int ray_tri(const double *x, const double *v, const double *a, const double *b,
-                   const double *c, double *t)
+                   const double *c, double tmin, double *t)
 {
     double e1[3], e2[3], pv[3], tv[3], qv[3];
     sub(3, b, a, e1);
@@ -185,7 +185,7 @@ static int ray_tri(const double *x, const double *v, const double *a, const doub
     double w = dot(3, v, qv) * inv;
     if (w < 0 || u + w > 1) return 0;
     double tt = dot(3, e2, qv) * inv;
-    if (!(tt > 0)) return 0;
+    if (!(tt > tmin)) return 0;
     *t = tt;
     return 1;
 }
@@ -382,17 +382,39 @@ int orc_closest_silhouette(const orc_scene *s, const double *x, double *dist)
     return best;
 }
 
-int orc_ray_neumann(const orc_scene *s, const double *x, const double *v, double tmax, int skip,
-                    double *t)
+static int ray_neumann(const orc_scene *s, const double *x, const double *v, double tmax, int skip,
+                       int exit_only, double *t)
 {
+    /* exit casts: rounding band of a position, 16 units of 2^-24 of the
+       scene scale */
+    const double band = 16.0 * ldexp(1.0, -24) * s->scale;
+    const int d = s->dim;
     int best = -1;
     double bt = INFINITY;
     for (int i = 0; i < s->nprims; ++i) {
         if (s->bc[i] != 1 || i == skip) continue;
-        const int32_t *p = s->P + (size_t)i * s->dim;
+        const int32_t *p = s->P + (size_t)i * d;
         double tt;
-        int hit = s->dim == 2 ? ray_seg(x, v, vert(s, p[0]), vert(s, p[1]), &tt)
-                              : ray_tri(x, v, vert(s, p[0]), vert(s, p[1]), vert(s, p[2]), &tt);
+        int hit;
+        if (exit_only) {
+            /* the ray leaves the domain through primitive i iff it points
+               against the inward normal and crosses the primitive's line /
+               plane at t > -band within distance band of the primitive (a
+               walk standing within rounding of a vertex that heads out
+               through the next primitive crosses it at t ~ 0) */
+            double ng[3], am[3], q[3], qc[3];
+            orc_inward_normal(s, i, ng);
+            double vn = dot(d, v, ng);
+            if (!(vn < 0)) continue;
+            sub(d, vert(s, p[0]), x, am);
+            tt = dot(d, am, ng) / vn;
+            if (!(tt > -band)) continue;
+            for (int k = 0; k < d; ++k) q[k] = x[k] + tt * v[k];
+            hit = prim_closest(s, i, q, qc) <= band;
+        } else {
+            hit = d == 2 ? ray_seg(x, v, vert(s, p[0]), vert(s, p[1]), 0.0, &tt)
+                         : ray_tri(x, v, vert(s, p[0]), vert(s, p[1]), vert(s, p[2]), 0.0, &tt);
+        }
         if (hit && tt <= tmax && tt < bt) {
             bt = tt;
             best = i;
@@ -400,6 +422,18 @@ int orc_ray_neumann(const orc_scene *s, const double *x, const double *v, double
     }
     *t = bt;
     return best;
+}
+
+int orc_ray_neumann(const orc_scene *s, const double *x, const double *v, double tmax, int skip,
+                    double *t)
+{
+    return ray_neumann(s, x, v, tmax, skip, 0, t);
+}
+
+int orc_ray_neumann_exit(const orc_scene *s, const double *x, const double *v, double tmax, int skip,
+                         double *t)
+{
+    return ray_neumann(s, x, v, tmax, skip, 1, t);
 }
 
 double orc_winding(const orc_scene *s, const double *x)

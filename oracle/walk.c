@@ -154,7 +154,7 @@ double orc_walk(const orc_scene *s, const orc_field *fld, const orc_params *p, u
             uniform_dir(d, u[0], u[1], vs);
             if (on_neu && vdot(d, vs, n) < 0) reflect(d, vs, n, vs);
             double rho = d == 2 ? r * sqrt(u[2] * u[3]) : r * beta22_inv(u[2]);
-            if (orc_ray_neumann(s, x, vs, rho, on_neu ? prim : -1, &t) < 0) {
+            if (orc_ray_neumann_exit(s, x, vs, rho, on_neu ? prim : -1, &t) < 0) {
                 double y[3];
                 for (int i = 0; i < d; ++i) y[i] = x[i] + rho * vs[i];
                 S = -(r * r / (2.0 * d)) * orc__eval_f(s, y);
@@ -220,13 +220,14 @@ double orc_walk(const orc_scene *s, const orc_field *fld, const orc_params *p, u
 
         /* next point on the star boundary */
         double t;
-        int hit = orc_ray_neumann(s, x, nu, r, on_neu ? prim : -1, &t);
+        int hit = orc_ray_neumann_exit(s, x, nu, r, on_neu ? prim : -1, &t);
         if (hit >= 0) {
-            for (int i = 0; i < d; ++i) x[i] += t * nu[i];
-            double ng[3];
-            orc_inward_normal(s, hit, ng);
-            double sg = vdot(d, ng, nu) < 0 ? 1.0 : -1.0;
-            for (int i = 0; i < d; ++i) n[i] = sg * ng[i];
+            /* the walk stands at the hit point moved 16 * 2^-24 * scale along
+               the primitive's inward normal, strictly inside the domain */
+            const double band = 16.0 * ldexp(1.0, -24) * orc_scene_scale(s);
+            t = fmax(t, 0.0);
+            orc_inward_normal(s, hit, n);
+            for (int i = 0; i < d; ++i) x[i] += t * nu[i] + band * n[i];
             on_neu = 1;
             prim = hit;
         } else {

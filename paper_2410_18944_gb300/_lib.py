@@ -58,6 +58,21 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Job(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("field", C.c_void_p), ("points", C.c_void_p), ("npoints", C.c_int64),
+                ("nwalks", C.c_int32), ("eps", C.c_double), ("maxsteps", C.c_int32), ("seed", C.c_uint64),
+                ("out_mean", C.c_void_p), ("out_var", C.c_void_p)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("ctas_per_sm", C.c_int32), ("flush_polls", C.c_int32), ("candidates", C.c_int32),
+                ("best_ms", C.c_double), ("worst_ms", C.c_double), ("walk_launches", C.c_int32),
+                ("train_steps", C.c_int32), ("graph_nodes", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)
@@ -91,6 +106,11 @@ SIGNATURES = {
     "wost_mixture_sample": (C.c_int, [C.c_int32, C.c_int32, _fp, _fp, _fp, _u32p, C.c_uint64, C.c_uint32,
                                       C.c_int64, _fp, _fp]),
     "wost_diag_umma": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _fp, _fp, _fp]),
+    "wost_batch_create": (C.c_int, [C.c_int32, C.POINTER(Job), C.c_int32, C.POINTER(Exec), C.POINTER(_vp)]),
+    "wost_batch_run": (C.c_int, [_vp, _vp, C.POINTER(Stats)]),
+    "wost_batch_info_get": (C.c_int, [_vp, C.POINTER(BatchInfo)]),
+    "wost_batch_destroy": (C.c_int, [_vp]),
+    "wost_solve_batch": (C.c_int, [C.c_int32, C.POINTER(Job), C.c_int32, C.POINTER(Exec), C.POINTER(Stats)]),
     "wost_solve_plain_static": (C.c_int, [_vp, _vp, C.c_int64, C.c_int32, C.c_double, C.c_int32, C.c_uint64, _vp,
                                           _vp, _vp, _i64p]),
 }

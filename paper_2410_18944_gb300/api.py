@@ -228,6 +228,86 @@ def solve(scene: Scene, points, nwalks, eps=1e-3, maxsteps=128, guided=False, fi
     return mean, var, st.as_dict()
 
 
+def _job_array(jobs, with_var):
+    """ctypes wost_job array for job dicts; returns (array, means, vars, keepalive)."""
+    import torch
+    arr = (L.Job * len(jobs))()
+    means, vars_, keep = [], [], []
+    for j, spec in enumerate(jobs):
+        pts = spec["points"]
+        if not _is_cuda_tensor(pts) or pts.dtype != torch.float64 or not pts.is_contiguous():
+            raise ValueError("batch points must be contiguous float64 CUDA tensors")
+        n = pts.shape[0]
+        m = torch.empty(n, dtype=torch.float64, device=pts.device)
+        v = torch.empty(n, dtype=torch.float64, device=pts.device) if with_var else None
+        keep += [pts, spec["scene"], spec.get("field")]
+        means.append(m)
+        vars_.append(v)
+        J = arr[j]
+        J.scene = spec["scene"]._h
+        J.field = spec["field"]._h if spec.get("field") is not None else None
+        J.points = pts.data_ptr()
+        J.npoints = n
+        J.nwalks = int(spec["nwalks"])
+        J.eps = float(spec.get("eps", 1e-3))
+        J.maxsteps = int(spec.get("maxsteps", 128))
+        J.seed = int(spec.get("seed", 1))
+        J.out_mean = m.data_ptr()
+        J.out_var = v.data_ptr() if v is not None else None
+    return arr, means, vars_, keep
+
+
+class Batch:
+    """wost_batch_create / wost_batch_run / wost_batch_destroy: many scenes in
+    one persistent launch, replayed from a captured CUDA graph.
+
+    ``jobs`` is a sequence of dicts with keys scene (Scene), points (torch
+    CUDA float64 tensor (n, dim)), nwalks, and optionally eps (1e-3),
+    maxsteps (128), seed (1), field (Field, guided batches).  The plan owns
+    the output tensors ``mean[j]`` / ``var[j]`` and keeps the points alive."""
+
+    def __init__(self, jobs, guided=False, with_var=True, **exec_kw):
+        self._h = None
+        lib = L.load()
+        self._jobs, self.mean, self.var, self._keep = _job_array(jobs, with_var)
+        e = exec_defaults(**exec_kw)
+        h = C.c_void_p()
+        check(lib.wost_batch_create(len(jobs), self._jobs, 1 if guided else 0, C.byref(e), C.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        """Replays the plan; returns the summed stats dict."""
+        st = Stats()
+        check(L.load().wost_batch_run(self._h, stream, C.byref(st)))
+        return st.as_dict()
+
+    def info(self):
+        bi = L.BatchInfo()
+        check(L.load().wost_batch_info_get(self._h, C.byref(bi)))
+        return bi.as_dict()
+
+    def close(self):
+        if self._h:
+            L.load().wost_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batch(jobs, guided=False, with_var=True, **exec_kw):
+    """wost_solve_batch (plan, run, release in one call): (means, vars, stats)."""
+    arr, means, vars_, keep = _job_array(jobs, with_var)
+    e = exec_defaults(**exec_kw)
+    st = Stats()
+    check(L.load().wost_solve_batch(len(jobs), arr, 1 if guided else 0, C.byref(e), C.byref(st)))
+    del keep
+    return means, vars_, st.as_dict()
+
+
 def mixture_eval(dim, mu, kappa, lam, nu):
     mu = np.ascontiguousarray(mu, np.float32)
     kappa = np.ascontiguousarray(kappa, np.float32)

@@ -193,6 +193,7 @@ extern "C" wost_status wost_create_field(const wost_field_desc *desc, wost_field
     if (e == cudaSuccess) e = cudaMemset(f->mlp_m, 0, nm * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(f->mlp_v, 0, nm * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(f->wimg, 0, kWImgBytes);
+    if (e == cudaSuccess) e = cudaMemset(f->loss_acc, 0, 2 * sizeof(double));
     if (e != cudaSuccess) { delete f; return cuda_status(e, "wost_create_field"); }
     if ((rc = refresh_inference_copy(f, 0)) != WOST_OK) { delete f; return rc; }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) { delete f; return cuda_status(e, "wost_create_field"); }
@@ -219,7 +220,7 @@ extern "C" wost_status wost_field_set_params(wost_field *f, const float *grid, c
     WOST_CUDA(cudaMemset(f->grid_v, 0, f->n_grid() * sizeof(float)));
     WOST_CUDA(cudaMemset(f->mlp_m, 0, f->n_mlp() * sizeof(float)));
     WOST_CUDA(cudaMemset(f->mlp_v, 0, f->n_mlp() * sizeof(float)));
-    f->adam_t = 0;
+    WOST_CUDA(cudaMemset(f->adam_step(), 0, sizeof(unsigned long long)));
     wost_status rc = refresh_inference_copy(f, 0);
     if (rc != WOST_OK) return rc;
     WOST_CUDA(cudaDeviceSynchronize());

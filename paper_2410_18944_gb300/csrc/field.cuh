@@ -213,14 +213,16 @@ struct wost_field {
     float *mlp32 = nullptr, *mlp_m = nullptr, *mlp_v = nullptr, *mlp_g = nullptr;  // W1|W2|W3|b3 (exchange layout)
     uint8_t *wimg = nullptr;
     float *b3pad = nullptr;
-    int adam_t = 0;
     // training records: final buffer (12 floats each) and per-slot scratch
     float *rec = nullptr;
     int64_t rec_cap = 0;
     unsigned long long *rec_ctr = nullptr;   // [0] count, [1] dropped
     float *scratch = nullptr;
     size_t scratch_bytes = 0;
-    float *loss_acc = nullptr;               // FP64 loss sum (8 bytes)
+    float *loss_acc = nullptr;               // [0] FP64 loss sum, [1] Adam step count (u64)
+    // the Adam step count lives on the device so that a captured graph of
+    // training steps advances it on every replay
+    unsigned long long *adam_step() const { return reinterpret_cast<unsigned long long *>(loss_acc) + 1; }
     int t_c_mode = 0, t_reflect = 1;         // MIS options of the records in the buffer
     float t_c_fixed = 0.5f;
     int64_t n_mlp() const {

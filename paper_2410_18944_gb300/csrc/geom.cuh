@@ -50,10 +50,12 @@ __device__ __forceinline__ void node_box_d2(const float4 *__restrict__ nodes, in
 }
 
 // entry/exit of the ray o + t v (inv = 1/v) with the two child boxes
+// (exit casts: from t > -pad, boxes grown by pad on every side, so that
+// crossings within the rounding band of a primitive are not pruned)
 template <int D>
 __device__ __forceinline__ void node_box_ray(const float4 *__restrict__ nodes, int node, const float *o,
                                              const float *inv, float tmax, float &t0, float &t1,
-                                             int &r0, int &r1) {
+                                             int &r0, int &r1, float pad = 0.f) {
     float lo0[3], hi0[3], lo1[3], hi1[3];
     if (D == 2) {
         const float4 a = __ldg(nodes + 3 * node), b = __ldg(nodes + 3 * node + 1), r = __ldg(nodes + 3 * node + 2);
@@ -69,11 +71,11 @@ __device__ __forceinline__ void node_box_ray(const float4 *__restrict__ nodes, i
         r0 = __float_as_int(r.x);
         r1 = __float_as_int(r.y);
     }
-    float e0 = 0.f, x0 = tmax, e1 = 0.f, x1 = tmax;
+    float e0 = -pad, x0 = tmax, e1 = -pad, x1 = tmax;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        float a0 = (lo0[k] - o[k]) * inv[k], b0 = (hi0[k] - o[k]) * inv[k];
-        float a1 = (lo1[k] - o[k]) * inv[k], b1 = (hi1[k] - o[k]) * inv[k];
+        float a0 = (lo0[k] - pad - o[k]) * inv[k], b0 = (hi0[k] + pad - o[k]) * inv[k];
+        float a1 = (lo1[k] - pad - o[k]) * inv[k], b1 = (hi1[k] + pad - o[k]) * inv[k];
         e0 = fmaxf(e0, fminf(a0, b0));
         x0 = fminf(x0, fmaxf(a0, b0));
         e1 = fmaxf(e1, fminf(a1, b1));
@@ -371,17 +373,33 @@ __device__ int closest_silhouette(const DevBVH &bv, const float *x, float tau, f
 }
 
 // ---- ray cast against Neumann primitives --------------------------------------
-template <int D>
-__device__ __forceinline__ bool ray_prim(const float4 *__restrict__ P, int s, const float *o, const float *v, float &t) {
+// kExit: count only primitives the ray leaves the domain through.  The
+// boundary is closed and oriented (2D: domain left of a -> b; 3D: triangles
+// counter-clockwise seen from outside), so from inside the domain the first
+// crossing is always such an exit; an entry hit can only come from a start
+// point that rounding put a hair outside the boundary, and taking it would
+// put the walker on the wrong side.  2D: exit iff cross(v, b - a) > 0;
+// 3D: exit iff v . ((b - a) x (c - a)) > 0, i.e. the Moller-Trumbore
+// determinant (b - a) . (v x (c - a)) is negative.  Exit hits count from
+// t > -tneg and within about tneg of the primitive (segment parameter /
+// barycentric slack tneg over the length / smallest height): a walker that
+// stands on a Neumann primitive within rounding of its end vertex and heads
+// out through the next primitive crosses it at t ~ 0, and rounding can put
+// that crossing slightly behind the start or past the primitive's end; a
+// start point inside the domain has no exit crossing behind it.
+template <int D, bool kExit = false>
+__device__ __forceinline__ bool ray_prim(const float4 *__restrict__ P, int s, const float *o, const float *v, float &t,
+                                         float tneg = 0.f) {
     if (D == 2) {
         float4 p = __ldg(P + s);
         float ex = p.z - p.x, ey = p.w - p.y;
         float ax = p.x - o[0], ay = p.y - o[1];
         float den = v[0] * ey - v[1] * ex;
-        if (den == 0.f) return false;
+        if (kExit ? !(den > 0.f) : den == 0.f) return false;
         float tt = (ax * ey - ay * ex) / den;
         float ss = (ax * v[1] - ay * v[0]) / den;
-        if (ss < 0.f || ss > 1.f || !(tt > 0.f)) return false;
+        const float eta = kExit ? tneg * rsqrtf(ex * ex + ey * ey) : 0.f;
+        if (ss < -eta || ss > 1.f + eta || !(tt > (kExit ? -tneg : 0.f))) return false;
         t = tt;
         return true;
     } else {
@@ -390,32 +408,42 @@ __device__ __forceinline__ bool ray_prim(const float4 *__restrict__ P, int s, co
         float e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
         float pv[3] = {v[1] * e2[2] - v[2] * e2[1], v[2] * e2[0] - v[0] * e2[2], v[0] * e2[1] - v[1] * e2[0]};
         float det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
-        if (det == 0.f) return false;
+        if (kExit ? !(det < 0.f) : det == 0.f) return false;
+        float eta = 0.f;
+        if (kExit) {
+            float n0 = e1[1] * e2[2] - e1[2] * e2[1], n1 = e1[2] * e2[0] - e1[0] * e2[2], n2 = e1[0] * e2[1] - e1[1] * e2[0];
+            float e3[3] = {e2[0] - e1[0], e2[1] - e1[1], e2[2] - e1[2]};
+            float l2 = fmaxf(fmaxf(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2], e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]),
+                             e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2]);
+            eta = tneg * sqrtf(l2) * rsqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+        }
         float inv = 1.f / det;
         float tv[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
         float u = (tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2]) * inv;
-        if (u < 0.f || u > 1.f) return false;
+        if (u < -eta || u > 1.f + eta) return false;
         float qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2], tv[0] * e1[1] - tv[1] * e1[0]};
         float w = (v[0] * qv[0] + v[1] * qv[1] + v[2] * qv[2]) * inv;
-        if (w < 0.f || u + w > 1.f) return false;
+        if (w < -eta || u + w > 1.f + eta) return false;
         float tt = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * inv;
-        if (!(tt > 0.f)) return false;
+        if (!(tt > (kExit ? -tneg : 0.f))) return false;
         t = tt;
         return true;
     }
 }
 
 // FP64 re-test of a hit: the same intersection in double precision
-template <int D>
-__device__ __forceinline__ bool ray_prim64(const DevBVH &bv, int s, const float *of, const float *vf, double &t) {
+template <int D, bool kExit = false>
+__device__ __forceinline__ bool ray_prim64(const DevBVH &bv, int s, const float *of, const float *vf, double &t,
+                                           double tneg = 0.0) {
     double o[3] = {of[0], of[1], D == 3 ? of[2] : 0.0}, v[3] = {vf[0], vf[1], D == 3 ? vf[2] : 0.0};
     if (D == 2) {
         const double *p = bv.prims64 + 4 * (size_t)s;
         double ex = p[2] - p[0], ey = p[3] - p[1], ax = p[0] - o[0], ay = p[1] - o[1];
         double den = v[0] * ey - v[1] * ex;
-        if (den == 0.0) return false;
+        if (kExit ? !(den > 0.0) : den == 0.0) return false;
         double tt = (ax * ey - ay * ex) / den, ss = (ax * v[1] - ay * v[0]) / den;
-        if (ss < 0.0 || ss > 1.0 || !(tt > 0.0)) return false;
+        const double eta = kExit ? tneg / sqrt(ex * ex + ey * ey) : 0.0;
+        if (ss < -eta || ss > 1.0 + eta || !(tt > (kExit ? -tneg : 0.0))) return false;
         t = tt;
         return true;
     } else {
@@ -423,25 +451,34 @@ __device__ __forceinline__ bool ray_prim64(const DevBVH &bv, int s, const float 
         double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
         double pv[3] = {v[1] * e2[2] - v[2] * e2[1], v[2] * e2[0] - v[0] * e2[2], v[0] * e2[1] - v[1] * e2[0]};
         double det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
-        if (det == 0.0) return false;
+        if (kExit ? !(det < 0.0) : det == 0.0) return false;
+        double eta = 0.0;
+        if (kExit) {
+            double n0 = e1[1] * e2[2] - e1[2] * e2[1], n1 = e1[2] * e2[0] - e1[0] * e2[2], n2 = e1[0] * e2[1] - e1[1] * e2[0];
+            double e3[3] = {e2[0] - e1[0], e2[1] - e1[1], e2[2] - e1[2]};
+            double l2 = fmax(fmax(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2], e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]),
+                             e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2]);
+            eta = tneg * sqrt(l2 / (n0 * n0 + n1 * n1 + n2 * n2));
+        }
         double inv = 1.0 / det;
         double tv[3] = {o[0] - a[0], o[1] - a[1], o[2] - a[2]};
         double u = (tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2]) * inv;
-        if (u < 0.0 || u > 1.0) return false;
+        if (u < -eta || u > 1.0 + eta) return false;
         double qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2], tv[0] * e1[1] - tv[1] * e1[0]};
         double w = (v[0] * qv[0] + v[1] * qv[1] + v[2] * qv[2]) * inv;
-        if (w < 0.0 || u + w > 1.0) return false;
+        if (w < -eta || u + w > 1.0 + eta) return false;
         double tt = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * inv;
-        if (!(tt > 0.0)) return false;
+        if (!(tt > (kExit ? -tneg : 0.0))) return false;
         t = tt;
         return true;
     }
 }
 
-// first Neumann hit with 0 < t <= tmax, skipping leaf slot `skip`; returns slot or -1
-template <int D>
+// first Neumann hit with 0 < t <= tmax, skipping leaf slot `skip`; returns
+// slot or -1 (kExit: exit hits only, from t > -tneg, see ray_prim)
+template <int D, bool kExit = false>
 __device__ int ray_neumann(const DevBVH &bv, const float *o, const float *v, float tmax, int skip, float &thit,
-                           int *err, Visits *vis = nullptr) {
+                           int *err, Visits *vis = nullptr, float tneg = 0.f) {
     thit = tmax;
     if (bv.nprims == 0) return -1;
     const unsigned mask = __activemask();
@@ -462,7 +499,7 @@ __device__ int ray_neumann(const DevBVH &bv, const float *o, const float *v, flo
             bool pop = false;
             float t0, t1;
             int r0, r1;
-            node_box_ray<D>(bv.nodes, ref, o, inv, best, t0, t1, r0, r1);
+            node_box_ray<D>(bv.nodes, ref, o, inv, best, t0, t1, r0, r1, kExit ? tneg : 0.f);
             if (vis) vis->nodes++;
             bool h0 = t0 <= best, h1 = t1 <= best;
             if (h0 && h1) {
@@ -484,7 +521,7 @@ __device__ int ray_neumann(const DevBVH &bv, const float *o, const float *v, flo
             if (vis) vis->nprims += cnt;
             for (int s = s0; s < s0 + cnt; ++s) {
                 float t;
-                if (s != skip && ray_prim<D>(bv.prims, s, o, v, t) && t <= best) {
+                if (s != skip && ray_prim<D, kExit>(bv.prims, s, o, v, t, tneg) && t <= best) {
                     int id = __ldg(bv.ids + s);
                     if (t < best || id < best_id) { best = t; best_slot = s; best_id = id; }
                 }

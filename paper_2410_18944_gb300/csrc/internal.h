@@ -74,6 +74,9 @@ struct CallTiming {
 };
 // launch helpers implemented in walk.cu
 int num_sms();
+// algorithmic bytes of walk launches from their statistics hs[0..6]
+// (walk-steps, truncated, walks, node / Dirichlet / silhouette / Neumann visits)
+double walk_alg_bytes(int D, bool guided, const unsigned long long *hs, int64_t records);
 int *device_err_flag();                  // device word: bit 0 stack overflow, bit 1 wait timeout
 wost_status device_check(cudaStream_t st);
 }

@@ -1,0 +1,191 @@
+// Where a walk's work comes from.  The persistent walk loops (plain here,
+// guided in guided_ws.cuh) are written once against a "job source":
+//   SoloSrc  - one scene, one point set, one field: everything lives in the
+//              kernel's argument block (wost_solve);
+//   BatchSrc - many scenes of uneven size, each with its own points, walk
+//              count, eps, step cap, seed and field, in a device job table
+//              (wost_solve_batch).  Work items are laid out job-major, so the
+//              walks in flight at any moment belong to few jobs.
+// A source hands out work items, starts a walk from an item, gives the
+// step its scene and scalars (StepEnv), and owns the per-point sums and the
+// training-record buffer the walk writes to.  Either way every walk draws
+// from the same Philox streams, counter (point, walk, step, purpose) and key
+// (seed_lo, seed_hi + scene_id), so a job of a batch walks exactly as the
+// same problem solved alone.
+#pragma once
+#include "field.cuh"
+#include "walkstep.cuh"
+
+namespace wost {
+
+constexpr int kRecFloats = 12;   // training record: x[3] nu[3] n[3] on_neumann q target
+
+// destination of finished training records (Sec. 5.2): buffer, counters
+// ([0] appended, [1] dropped), capacity
+struct RecDest {
+    float *out;
+    unsigned long long *ctr;
+    long long cap;
+};
+
+// ---------------------------------------------------------------------------
+// one scene
+// ---------------------------------------------------------------------------
+template <int D>
+struct SoloSrc {
+    const WalkArgs &a;
+    const DevField *f;   // guided only
+    RecDest rd;
+
+    __device__ __forceinline__ unsigned long long *work_ctr() const { return a.work_ctr; }
+    __device__ __forceinline__ unsigned long long total() const { return a.total; }
+    __device__ __forceinline__ bool start(Walk<D> &w, unsigned long long item) const {
+        start_walk<D>(w, a, item);
+        return a.status[w.pid] == 0;
+    }
+    __device__ __forceinline__ StepEnv env(const Walk<D> &) const { return env_of(a); }
+    __device__ __forceinline__ void finish(const Walk<D> &w) const { finish_walk(a, w.pid, w.acc); }
+    __device__ __forceinline__ const DevField &field(const Walk<D> &) const { return *f; }
+    __device__ __forceinline__ RecDest rec(const Walk<D> &) const { return rd; }
+    __device__ __forceinline__ int job(const Walk<D> &) const { return 0; }
+    __device__ __forceinline__ const uint4 *wimg(int) const { return f->wimg; }
+    __device__ __forceinline__ const float *b3(int) const { return f->b3; }
+};
+
+// ---------------------------------------------------------------------------
+// many scenes
+// ---------------------------------------------------------------------------
+struct DevJob {
+    DevScene sc;
+    DevField f;                  // the job's field (guided batches)
+    const double *points;        // npoints * D (device)
+    int64_t npoints;
+    int64_t point_off;           // first row of the job in the batch's per-point arrays
+    int nwalks;
+    int maxsteps;
+    float eps;
+    double eps64;
+    uint32_t key0, key1;
+    RecDest rd;                  // the field's record buffer
+    double *out_mean, *out_var;  // npoints each (device; out_var nullable)
+};
+
+// a contiguous run of work items of one launch: walks [walk_begin,
+// walk_begin + n) of every point of one job, items ordered walk-major
+// within the run (item = walk * npoints + point)
+struct DevSeg {
+    unsigned long long item_begin;
+    int job;
+    int walk_begin;
+};
+
+struct BatchArgs {
+    const DevJob *jobs;
+    const DevSeg *segs;
+    int nseg;
+    unsigned long long total;        // items in this launch
+    unsigned long long *work_ctr;
+    const uint8_t *status;           // per point of the batch: 0 walk, 1 shell, 2 outside
+    double *sum, *sum2;              // per point of the batch (FP64)
+    unsigned long long *stat;        // launch statistics (as WalkArgs::stat)
+    int *err;
+};
+
+// index of the last segment whose item_begin <= item (segments sorted)
+__device__ __forceinline__ int find_seg(const DevSeg *segs, int nseg, unsigned long long item) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&segs[mid].item_begin) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int D>
+struct BatchSrc {
+    const BatchArgs &b;
+
+    __device__ __forceinline__ unsigned long long *work_ctr() const { return b.work_ctr; }
+    __device__ __forceinline__ unsigned long long total() const { return b.total; }
+    __device__ __forceinline__ bool start(Walk<D> &w, unsigned long long item) const {
+        const int s = find_seg(b.segs, b.nseg, item);
+        const DevSeg sg = b.segs[s];
+        const DevJob &J = b.jobs[sg.job];
+        const unsigned long long local = item - sg.item_begin, np = (unsigned long long)J.npoints;
+        w.job = sg.job;
+        w.pid = (uint32_t)(local % np);
+        w.wid = (uint32_t)(sg.walk_begin + local / np);
+#pragma unroll
+        for (int i = 0; i < D; ++i) { w.x[i] = (float)J.points[(size_t)w.pid * D + i]; w.n[i] = 0.f; }
+        w.T = 1.f;
+        w.acc = 0.f;
+        w.k = 0;
+        w.prim = -1;
+        return b.status[J.point_off + w.pid] == 0;
+    }
+    __device__ __forceinline__ StepEnv env(const Walk<D> &w) const {
+        const DevJob &J = b.jobs[w.job];
+        return StepEnv{J.sc, J.eps, J.eps64, J.maxsteps, J.key0, J.key1, b.err};
+    }
+    __device__ __forceinline__ void finish(const Walk<D> &w) const {
+        const size_t i = (size_t)b.jobs[w.job].point_off + w.pid;
+        atomicAdd(b.sum + i, (double)w.acc);
+        atomicAdd(b.sum2 + i, (double)w.acc * (double)w.acc);
+    }
+    __device__ __forceinline__ const DevField &field(const Walk<D> &w) const { return b.jobs[w.job].f; }
+    __device__ __forceinline__ RecDest rec(const Walk<D> &w) const { return b.jobs[w.job].rd; }
+    __device__ __forceinline__ int job(const Walk<D> &w) const { return w.job; }
+    __device__ __forceinline__ const uint4 *wimg(int j) const { return b.jobs[j].f.wimg; }
+    __device__ __forceinline__ const float *b3(int j) const { return b.jobs[j].f.b3; }
+};
+
+// ---------------------------------------------------------------------------
+// The plain persistent walk loop (uniform directions, Sec. 3.2).
+// Every lane of a warp stays in the loop until the whole warp is out of
+// work, and one loop iteration is one step of every active lane: lanes
+// cannot drift into different phases of the step, so the warp re-converges
+// after each query (a lane without a walk is predicated off).
+// ---------------------------------------------------------------------------
+template <int D, class Src>
+__device__ __forceinline__ void plain_loop(const Src &src, unsigned long long *stat) {
+    Walk<D> w;
+    Visits vis;
+    bool active = false, exhausted = false;
+    unsigned long long nsteps = 0, ntrunc = 0, nwalks = 0;
+    for (;;) {
+        if (!active && !exhausted) {
+            unsigned long long item = warp_fetch_add(src.work_ctr(), true);
+            if (item >= src.total()) exhausted = true;
+            else if (src.start(w, item)) { active = true; nwalks++; }
+        }
+        if (!__any_sync(0xffffffffu, active || !exhausted)) break;
+        __syncwarp();
+        if (!active) continue;
+        nsteps++;
+        const StepEnv env = src.env(w);
+        float r, S, gv;
+        bool trunc = false;
+        bool ended = step_geometry<D>(w, env, r, S, gv, trunc, &vis);
+        float nu[D];
+        if (!ended) {
+            U4 u = philox(w.pid, w.wid, (uint32_t)w.k, P_DIR, env.key0, env.key1);
+            uniform_dir<D>(u01(u.x), u01(u.y), nu);
+            if (w.prim >= 0) {
+                float dn = dotv<D>(nu, w.n);
+                if (dn < 0.f) reflect<D>(nu, w.n);
+                ended = dn == 0.f;   // zero density at the tangent plane (Eq. angular_req)
+            }
+        }
+        if (ended) {
+            src.finish(w);
+            ntrunc += trunc;
+            active = false;
+        } else {
+            step_move<D>(w, env, nu, r, &vis);
+        }
+    }
+    flush_stats(stat, nsteps, ntrunc, nwalks, vis);
+}
+
+}  // namespace wost

@@ -19,7 +19,7 @@
 #include <mutex>
 
 #include "internal.h"
-#include "walkstep.cuh"
+#include "jobsrc.cuh"
 
 namespace wost {
 namespace {
@@ -74,95 +74,25 @@ wost_status static_base(unsigned char **out) {
 }
 
 template <int D>
-__global__ void static_classify_kernel(WalkArgs a, double *shell) {
+__global__ void static_classify_kernel(WalkArgs a, double *shell_value) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.npoints) return;
-    float x[D];
-    for (int k = 0; k < D; ++k) x[k] = (float)a.points[i * D + k];
-    const float dir[3] = {0.5377844f, 0.7924136f, 0.2876523f};
-    float v[D], nn = 0.f;
-    for (int k = 0; k < D; ++k) { v[k] = dir[k]; nn += v[k] * v[k]; }
-    for (int k = 0; k < D; ++k) v[k] *= rsqrtf(nn);
-    int c = ray_count<D>(a.sc.dir, x, v, a.err) + ray_count<D>(a.sc.neu, x, v, a.err);
-    uint8_t st = 0;
-    double val = 0.0;
-    if ((c & 1) == 0) {
-        st = 2;
-        val = __longlong_as_double(0x7ff8000000000000LL);
-    } else {
-        float bd2;
-        int slot = closest_dirichlet<D>(a.sc.dir, x, bd2, a.err);
-        double q[3];
-        if (dirichlet_dist64<D>(a.sc.dir, slot, x, q) <= a.eps64) {
-            st = 1;
-            float xb[3] = {(float)q[0], (float)q[1], D == 3 ? (float)q[2] : 0.f};
-            val = eval_fn<D>(a.sc.g, xb);
-        }
-    }
-    const_cast<uint8_t *>(a.status)[i] = st;
-    shell[i] = val;
+    double val;
+    const_cast<uint8_t *>(a.status)[i] = classify_point<D>(a.sc, a.eps64, a.points + i * D, a.err, val);
+    shell_value[i] = val;
 }
 
 // the plain persistent walk loop, on the static scratch
 template <int D>
-__global__ void __launch_bounds__(128) static_walk_kernel(WalkArgs a) {
-    Walk<D> w;
-    Visits vis;
-    bool active = false, exhausted = false;
-    unsigned long long nsteps = 0, ntrunc = 0, nwalks = 0;
-    for (;;) {
-        if (!active && !exhausted) {
-            unsigned long long item = warp_fetch_add(a.work_ctr, true);
-            if (item >= a.total) {
-                exhausted = true;
-            } else {
-                start_walk<D>(w, a, item);
-                if (a.status[w.pid] == 0) { active = true; nwalks++; }
-            }
-        }
-        if (!__any_sync(0xffffffffu, active || !exhausted)) break;
-        __syncwarp();
-        if (!active) continue;
-        nsteps++;
-        float r, S, gv;
-        bool trunc = false;
-        bool ended = step_geometry<D>(w, a, r, S, gv, trunc, &vis);
-        float nu[D];
-        if (!ended) {
-            U4 u = philox(w.pid, w.wid, (uint32_t)w.k, P_DIR, a.key0, a.key1);
-            uniform_dir<D>(u01(u.x), u01(u.y), nu);
-            if (w.prim >= 0) {
-                float dn = dotv<D>(nu, w.n);
-                if (dn < 0.f) reflect<D>(nu, w.n);
-                ended = dn == 0.f;
-            }
-        }
-        if (ended) {
-            finish_walk(a, w.pid, w.acc);
-            ntrunc += trunc;
-            active = false;
-        } else {
-            step_move<D>(w, a, nu, r, &vis);
-        }
-    }
-    flush_counters(a, nsteps, ntrunc, nwalks, vis);
+__global__ void __launch_bounds__(128) static_walk_kernel(const __grid_constant__ WalkArgs a) {
+    plain_loop<D>(SoloSrc<D>{a, nullptr, RecDest{}}, a.stat);
 }
 
-__global__ void static_finalize_kernel(const uint8_t *status, const double *shell, const double *sum,
-                                       const double *sum2, int64_t n, int nw, double *mean, double *var) {
+__global__ void static_finalize_kernel(const uint8_t *status, const double *shell_value, const double *sum,
+                                const double *sum2, int64_t n, int nw, double *mean, double *var) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (status[i] != 0) {
-        mean[i] = shell[i];
-        if (var) var[i] = status[i] == 1 ? 0.0 : shell[i];
-        return;
-    }
-    double m = sum[i] / nw;
-    mean[i] = m;
-    if (var) {
-        double v = nw > 1 ? (sum2[i] - nw * m * m) / ((double)nw * (nw - 1)) : 0.0;
-        var[i] = v > 0 ? v : 0.0;
-    }
+    finalize_point(status[i], shell_value[i], sum[i], sum2[i], nw, mean + i, var ? var + i : nullptr);
 }
 
 }  // namespace

@@ -330,16 +330,33 @@ __global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
 }
 
 // Adam on a flat FP32 array
-__global__ void adam_kernel(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
-                            float eps, float c1, float c2) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float gi = g[i];
-    float mi = b1 * m[i] + (1.f - b1) * gi;
-    float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+// Adam (Kingma & Ba) over the grid and the MLP parameters in one launch:
+// blocks [0, nb_grid) update the grid, the rest the MLP; the step count t is
+// read from the device (advanced by adam_tick_kernel just before)
+struct AdamGroup {
+    float *p;
+    const float *g;
+    float *m, *v;
+    int64_t n;
+    float lr;
+};
+
+__global__ void adam_tick_kernel(unsigned long long *t) { *t += 1; }
+
+__global__ void adam_kernel(AdamGroup ga, AdamGroup gb, int nb_a, float b1, float b2, float eps,
+                            const unsigned long long *t_dev) {
+    const bool first = (int)blockIdx.x < nb_a;
+    const AdamGroup &G = first ? ga : gb;
+    int64_t i = (int64_t)(first ? blockIdx.x : blockIdx.x - nb_a) * blockDim.x + threadIdx.x;
+    if (i >= G.n) return;
+    const float t = (float)*t_dev;
+    const float c1 = 1.f - powf(b1, t), c2 = 1.f - powf(b2, t);
+    float gi = G.g[i];
+    float mi = b1 * G.m[i] + (1.f - b1) * gi;
+    float vi = b2 * G.v[i] + (1.f - b2) * gi * gi;
+    G.m[i] = mi;
+    G.v[i] = vi;
+    G.p[i] -= G.lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
 __global__ void grid_to_half_kernel(const float *g32, __half2 *g16, int64_t n) {
@@ -376,6 +393,19 @@ wost_status refresh_inference_copy(wost_field *f, cudaStream_t st) {
     return WOST_OK;
 }
 
+// one-time kernel attributes (also called before a stream capture, where
+// the launches follow without further set-up)
+wost_status train_prepare(int dim) {
+    static bool attr[4] = {false, false, false, false};
+    if (dim != 2 && dim != 3) return WOST_ERR_INVALID_ARG;
+    if (!attr[dim]) {
+        if (dim == 2) WOST_CUDA(cudaFuncSetAttribute(train_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem));
+        else WOST_CUDA(cudaFuncSetAttribute(train_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem));
+        attr[dim] = true;
+    }
+    return WOST_OK;
+}
+
 // gradient of the mean loss over the record buffer into f->grid_g / f->mlp_g
 wost_status train_grad_launch(wost_field *f, int dim, cudaStream_t st) {
     WOST_CUDA(cudaMemsetAsync(f->grid_g, 0, f->n_grid() * sizeof(float), st));
@@ -398,15 +428,10 @@ wost_status train_grad_launch(wost_field *f, int dim, cudaStream_t st) {
     a.loss_acc = reinterpret_cast<double *>(f->loss_acc);
     a.err = device_err_flag();
     // one CTA per SM: each CTA holds all 512 TMEM columns of its SM
-    int grid = num_sms();
-    static bool attr2 = false, attr3 = false;
-    if (dim == 2) {
-        if (!attr2) { WOST_CUDA(cudaFuncSetAttribute(train_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem)); attr2 = true; }
-        train_kernel<2><<<grid, kTrainBlock, kTrainSmem, st>>>(a);
-    } else {
-        if (!attr3) { WOST_CUDA(cudaFuncSetAttribute(train_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem)); attr3 = true; }
-        train_kernel<3><<<grid, kTrainBlock, kTrainSmem, st>>>(a);
-    }
+    wost_status rc = train_prepare(dim);
+    if (rc != WOST_OK) return rc;
+    if (dim == 2) train_kernel<2><<<num_sms(), kTrainBlock, kTrainSmem, st>>>(a);
+    else train_kernel<3><<<num_sms(), kTrainBlock, kTrainSmem, st>>>(a);
     WOST_CUDA(cudaGetLastError());
     return WOST_OK;
 }
@@ -414,14 +439,13 @@ wost_status train_grad_launch(wost_field *f, int dim, cudaStream_t st) {
 wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *) {
     wost_status rc = train_grad_launch(f, dim, st);
     if (rc != WOST_OK || !apply_adam) return rc;
-    f->adam_t++;
     const wost_field_desc &d = f->desc;
-    float c1 = 1.f - powf(d.beta1, (float)f->adam_t), c2 = 1.f - powf(d.beta2, (float)f->adam_t);
     int64_t ng = f->n_grid(), nm = f->n_mlp();
-    adam_kernel<<<(int)((ng + 255) / 256), 256, 0, st>>>(f->grid32, f->grid_g, f->grid_m, f->grid_v, ng, d.lr_grid,
-                                                         d.beta1, d.beta2, d.adam_eps, c1, c2);
-    adam_kernel<<<(int)((nm + 255) / 256), 256, 0, st>>>(f->mlp32, f->mlp_g, f->mlp_m, f->mlp_v, nm, d.lr_mlp,
-                                                         d.beta1, d.beta2, d.adam_eps, c1, c2);
+    AdamGroup ga{f->grid32, f->grid_g, f->grid_m, f->grid_v, ng, d.lr_grid};
+    AdamGroup gb{f->mlp32, f->mlp_g, f->mlp_m, f->mlp_v, nm, d.lr_mlp};
+    const int nba = (int)((ng + 255) / 256), nbb = (int)((nm + 255) / 256);
+    adam_tick_kernel<<<1, 1, 0, st>>>(f->adam_step());
+    adam_kernel<<<nba + nbb, 256, 0, st>>>(ga, gb, nba, d.beta1, d.beta2, d.adam_eps, f->adam_step());
     WOST_CUDA(cudaGetLastError());
     return refresh_inference_copy(f, st);
 }

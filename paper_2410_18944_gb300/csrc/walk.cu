@@ -15,9 +15,22 @@
 
 #include "field.cuh"
 #include "internal.h"
-#include "walkstep.cuh"
+#include "jobsrc.cuh"
 
 namespace wost {
+
+double walk_alg_bytes(int D, bool guided, const unsigned long long *hs, int64_t records) {
+    // bytes per item of the leaf-order arrays (see common.cuh)
+    const double node_b = D == 2 ? 48 : 64, prim_b = D == 2 ? 16 : 48, sil_b = D == 2 ? 32 : 64;
+    double b = hs[3] * node_b + hs[4] * prim_b + hs[5] * sil_b + hs[6] * prim_b;
+    b += (double)hs[2] * (D * 8.0 + 2 * 8.0);          // start point, FP64 sum and sum of squares
+    if (guided) {
+        double decodes = (double)hs[0] - (double)hs[2];  // every non-terminal step decodes once
+        b += decodes * 16.0 * (1 << D) * 4.0;            // L = 16 levels x 2^d corners x 2 FP16
+        b += (double)records * (48.0 + 48.0 + 48.0);     // record write, suffix read, final write
+    }
+    return b;
+}
 
 int num_sms() {
     static int n = 0;
@@ -54,51 +67,8 @@ void DevBuf::release() {
 constexpr int kPlainBlock = 128;
 
 template <int D>
-__global__ void __launch_bounds__(kPlainBlock) plain_walk_kernel(WalkArgs a) {
-    // Every lane of a warp stays in the loop until the whole warp is out of
-    // work, and one loop iteration is one step of every active lane: lanes
-    // cannot drift into different phases of the step, so the warp re-converges
-    // after each query (a lane without a walk is predicated off).
-    Walk<D> w;
-    Visits vis;
-    bool active = false, exhausted = false;
-    unsigned long long nsteps = 0, ntrunc = 0, nwalks = 0;
-    for (;;) {
-        if (!active && !exhausted) {
-            unsigned long long item = warp_fetch_add(a.work_ctr, true);
-            if (item >= a.total) {
-                exhausted = true;
-            } else {
-                start_walk<D>(w, a, item);
-                if (a.status[w.pid] == 0) { active = true; nwalks++; }
-            }
-        }
-        if (!__any_sync(0xffffffffu, active || !exhausted)) break;
-        __syncwarp();
-        if (!active) continue;
-        nsteps++;
-        float r, S, gv;
-        bool trunc = false;
-        bool ended = step_geometry<D>(w, a, r, S, gv, trunc, &vis);
-        float nu[D];
-        if (!ended) {
-            U4 u = philox(w.pid, w.wid, (uint32_t)w.k, P_DIR, a.key0, a.key1);
-            uniform_dir<D>(u01(u.x), u01(u.y), nu);
-            if (w.prim >= 0) {
-                float dn = dotv<D>(nu, w.n);
-                if (dn < 0.f) reflect<D>(nu, w.n);
-                ended = dn == 0.f;   // zero density at the tangent plane (Eq. angular_req)
-            }
-        }
-        if (ended) {
-            finish_walk(a, w.pid, w.acc);
-            ntrunc += trunc;
-            active = false;
-        } else {
-            step_move<D>(w, a, nu, r, &vis);
-        }
-    }
-    flush_counters(a, nsteps, ntrunc, nwalks, vis);
+__global__ void __launch_bounds__(kPlainBlock) plain_walk_kernel(const __grid_constant__ WalkArgs a) {
+    plain_loop<D>(SoloSrc<D>{a, nullptr, RecDest{}}, a.stat);
 }
 
 // status of every query point: 2 outside (odd/even crossing count of a ray
@@ -107,31 +77,8 @@ template <int D>
 __global__ void classify_kernel(WalkArgs a, double *shell_value) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.npoints) return;
-    float x[D];
-    for (int k = 0; k < D; ++k) x[k] = (float)a.points[i * D + k];
-    const float dir[3] = {0.5377844f, 0.7924136f, 0.2876523f};
-    float v[D];
-    float nn = 0;
-    for (int k = 0; k < D; ++k) { v[k] = dir[k]; nn += v[k] * v[k]; }
-    for (int k = 0; k < D; ++k) v[k] *= rsqrtf(nn);
-    int c = ray_count<D>(a.sc.dir, x, v, a.err) + ray_count<D>(a.sc.neu, x, v, a.err);
-    uint8_t st = 0;
-    double val = 0;
-    if ((c & 1) == 0) {
-        st = 2;
-        val = __longlong_as_double(0x7ff8000000000000LL);
-    } else {
-        float bd2;
-        int slot = closest_dirichlet<D>(a.sc.dir, x, bd2, a.err);
-        double q[3];
-        double dD = dirichlet_dist64<D>(a.sc.dir, slot, x, q);
-        if (dD <= a.eps64) {
-            st = 1;
-            float xb[3] = {(float)q[0], (float)q[1], D == 3 ? (float)q[2] : 0.f};
-            val = eval_fn<D>(a.sc.g, xb);
-        }
-    }
-    const_cast<uint8_t *>(a.status)[i] = st;
+    double val;
+    const_cast<uint8_t *>(a.status)[i] = classify_point<D>(a.sc, a.eps64, a.points + i * D, a.err, val);
     shell_value[i] = val;
 }
 
@@ -139,17 +86,7 @@ __global__ void finalize_kernel(const uint8_t *status, const double *shell_value
                                 const double *sum2, int64_t n, int nw, double *mean, double *var) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (status[i] != 0) {
-        mean[i] = shell_value[i];
-        if (var) var[i] = status[i] == 1 ? 0.0 : shell_value[i];
-        return;
-    }
-    double m = sum[i] / nw;
-    mean[i] = m;
-    if (var) {
-        double v = nw > 1 ? (sum2[i] - nw * m * m) / ((double)nw * (nw - 1)) : 0.0;
-        var[i] = v > 0 ? v : 0.0;
-    }
+    finalize_point(status[i], shell_value[i], sum[i], sum2[i], nw, mean + i, var ? var + i : nullptr);
 }
 
 // ---- query kernels -----------------------------------------------------------
@@ -362,16 +299,7 @@ extern "C" wost_status wost_solve(wost_scene *s, wost_field *field, const double
         stats->walks = (int64_t)hs[2];
         stats->node_visits = (int64_t)hs[3];
         stats->prim_visits = (int64_t)(hs[4] + hs[5] + hs[6]);
-        // bytes per item of the leaf-order arrays (see common.cuh)
-        const double node_b = D == 2 ? 48 : 64, prim_b = D == 2 ? 16 : 48, sil_b = D == 2 ? 32 : 64;
-        double b = hs[3] * node_b + hs[4] * prim_b + hs[5] * sil_b + hs[6] * prim_b;
-        b += (double)hs[2] * (D * 8.0 + 2 * 8.0);          // start point, FP64 sum and sum of squares
-        if (guided) {
-            double decodes = (double)hs[0] - (double)hs[2];  // every non-terminal step decodes once
-            b += decodes * 16.0 * (1 << D) * 4.0;            // L = 16 levels x 2^d corners x 2 FP16
-            b += (double)stats->records * (48.0 + 48.0 + 48.0);  // record write, suffix read, final write
-        }
-        stats->alg_bytes = b;
+        stats->alg_bytes = walk_alg_bytes(D, guided, hs, stats->records);
         stats->ms_walk = CallTiming::sum(tm.walk);
         stats->ms_train = CallTiming::sum(tm.train);
         stats->kernel_launches = tm.launches;

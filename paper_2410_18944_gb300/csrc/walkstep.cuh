@@ -34,12 +34,28 @@ struct WalkArgs {
     int *err;
 };
 
+// what one step needs besides the walk state: the walk's scene and the
+// solve's scalars (scene and keys differ per job in a multi-scene batch)
+struct StepEnv {
+    const DevScene &sc;
+    float eps;
+    double eps64;
+    int maxsteps;
+    uint32_t key0, key1;
+    int *err;
+};
+
+__device__ __forceinline__ StepEnv env_of(const WalkArgs &a) {
+    return StepEnv{a.sc, a.eps, a.eps64, a.maxsteps, a.key0, a.key1, a.err};
+}
+
 template <int D>
 struct Walk {
     float x[D], n[D];
     float T, acc;
     uint32_t pid, wid;
     int k, prim;     // prim: Neumann leaf slot the walker stands on, -1 if interior
+    int job;         // job of a multi-scene batch (unused by single solves)
 };
 
 template <int D>
@@ -98,7 +114,7 @@ __device__ __forceinline__ void finish_walk(const WalkArgs &a, uint32_t pid, flo
 // Steps 1-3.  Returns true if the walk ended (its value already added).
 // On return false: r (star radius) and S (this step's source term).
 template <int D>
-__device__ __forceinline__ bool step_geometry(Walk<D> &w, const WalkArgs &a, float &r, float &S,
+__device__ __forceinline__ bool step_geometry(Walk<D> &w, const StepEnv &a, float &r, float &S,
                                               float &term_value, bool &truncated, Visits *vis) {
     const DevScene &sc = a.sc;
     float bd2;
@@ -134,10 +150,11 @@ __device__ __forceinline__ bool step_geometry(Walk<D> &w, const WalkArgs &a, flo
         if (w.prim >= 0 && dotv<D>(vs, w.n) < 0.f) reflect<D>(vs, w.n);
         float rho = D == 2 ? r * sqrtf(u01(u.z) * u01(u.w)) : r * beta22_inv(u01(u.z));
         float th;
-        int hs = ray_neumann<D>(sc.neu, w.x, vs, rho, w.prim, th, a.err, vis);
+        const float tneg = kRoundBand * sc.scale;
+        int hs = ray_neumann<D, true>(sc.neu, w.x, vs, rho, w.prim, th, a.err, vis, tneg);
         if (hs >= 0 && rho - th <= kRoundBand * (sc.scale + rho)) {
             double t64;
-            if (!ray_prim64<D>(sc.neu, hs, w.x, vs, t64) || t64 > (double)rho) hs = -1;
+            if (!ray_prim64<D, true>(sc.neu, hs, w.x, vs, t64, tneg) || t64 > (double)rho) hs = -1;
         }
         if (hs < 0) {
             float y[3];
@@ -152,23 +169,32 @@ __device__ __forceinline__ bool step_geometry(Walk<D> &w, const WalkArgs &a, flo
 
 // Step 5: ray cast within r and move.
 template <int D>
-__device__ __forceinline__ void step_move(Walk<D> &w, const WalkArgs &a, const float *nu, float r, Visits *vis) {
+__device__ __forceinline__ void step_move(Walk<D> &w, const StepEnv &a, const float *nu, float r, Visits *vis) {
     const DevScene &sc = a.sc;
     float th;
-    int hit = ray_neumann<D>(sc.neu, w.x, nu, r, w.prim, th, a.err, vis);
+    // the first exit through the Neumann boundary (ray_prim, kExit), from
+    // t > -(rounding band of a position)
+    const float tneg = kRoundBand * sc.scale;
+    int hit = ray_neumann<D, true>(sc.neu, w.x, nu, r, w.prim, th, a.err, vis, tneg);
     // hit-or-reach-r decision: in FP64 when the FP32 hit lies within its
     // rounding band below r
     if (hit >= 0 && r - th <= kRoundBand * (sc.scale + r)) {
         double t64;
-        if (!ray_prim64<D>(sc.neu, hit, w.x, nu, t64) || t64 > (double)r) hit = -1;
+        if (!ray_prim64<D, true>(sc.neu, hit, w.x, nu, t64, tneg) || t64 > (double)r) hit = -1;
     }
     if (hit >= 0) {
-        float ng[D];
+        // an exit hit arrives from the inside, the side the walk is on, so
+        // the walker's normal is the primitive's inward normal (Sec. 4.1,
+        // normal convention at Eq. angular_req).  The walker stands at the
+        // hit point moved tneg along that normal: a rounded hit point may lie
+        // on either side of the boundary, and every later query (silhouettes,
+        // exit casts near a vertex) needs a start point inside the domain.
+        th = fmaxf(th, 0.f);
 #pragma unroll
-        for (int i = 0; i < D; ++i) { w.x[i] += th * nu[i]; ng[i] = __ldg(sc.nin_neu + (size_t)hit * D + i); }
-        float sg = dotv<D>(ng, nu) < 0.f ? 1.f : -1.f;
-#pragma unroll
-        for (int i = 0; i < D; ++i) w.n[i] = sg * ng[i];
+        for (int i = 0; i < D; ++i) {
+            w.n[i] = __ldg(sc.nin_neu + (size_t)hit * D + i);
+            w.x[i] += th * nu[i] + tneg * w.n[i];
+        }
         w.prim = hit;
     } else {
 #pragma unroll
@@ -178,9 +204,57 @@ __device__ __forceinline__ void step_move(Walk<D> &w, const WalkArgs &a, const f
     w.k++;
 }
 
+// Status of a query point: 2 outside (odd/even crossing count of a fixed
+// ray against all primitives), 1 inside the epsilon-shell (val = g at the
+// closest Dirichlet point, FP64 distance test), 0 to be walked.
+template <int D>
+__device__ __forceinline__ uint8_t classify_point(const DevScene &sc, double eps64, const double *p, int *err,
+                                                  double &val) {
+    float x[D];
+    for (int k = 0; k < D; ++k) x[k] = (float)p[k];
+    const float dir[3] = {0.5377844f, 0.7924136f, 0.2876523f};
+    float v[D], nn = 0.f;
+    for (int k = 0; k < D; ++k) { v[k] = dir[k]; nn += v[k] * v[k]; }
+    for (int k = 0; k < D; ++k) v[k] *= rsqrtf(nn);
+    int c = ray_count<D>(sc.dir, x, v, err) + ray_count<D>(sc.neu, x, v, err);
+    val = 0.0;
+    if ((c & 1) == 0) {
+        val = __longlong_as_double(0x7ff8000000000000LL);
+        return 2;
+    }
+    float bd2;
+    int slot = closest_dirichlet<D>(sc.dir, x, bd2, err);
+    double q[3];
+    if (dirichlet_dist64<D>(sc.dir, slot, x, q) <= eps64) {
+        float xb[3] = {(float)q[0], (float)q[1], D == 3 ? (float)q[2] : 0.f};
+        val = eval_fn<D>(sc.g, xb);
+        return 1;
+    }
+    return 0;
+}
+
+// mean and variance of the mean of one point from its FP64 sums (Sec. 3.2);
+// shell / outside points take their classification value
+__device__ __forceinline__ void finalize_point(uint8_t status, double shell, double sum, double sum2, int nw,
+                                               double *mean, double *var) {
+    if (status != 0) {
+        *mean = shell;
+        if (var) *var = status == 1 ? 0.0 : shell;
+        return;
+    }
+    double m = sum / nw;
+    *mean = m;
+    if (var) {
+        double v = nw > 1 ? (sum2 - nw * m * m) / ((double)nw * (nw - 1)) : 0.0;
+        *var = v > 0 ? v : 0.0;
+    }
+}
+
 // block-level sum of the per-thread counters into the launch statistics
-__device__ __forceinline__ void flush_counters(const WalkArgs &a, unsigned long long steps, unsigned long long trunc,
-                                               unsigned long long walks, const Visits &v) {
+// stat[0..6]: walk-steps, truncated, walks, node / Dirichlet / silhouette /
+// Neumann visits
+__device__ __forceinline__ void flush_stats(unsigned long long *stat, unsigned long long steps,
+                                            unsigned long long trunc, unsigned long long walks, const Visits &v) {
     __shared__ unsigned long long red[7];
     if (threadIdx.x < 7) red[threadIdx.x] = 0;
     __syncthreads();
@@ -192,7 +266,7 @@ __device__ __forceinline__ void flush_counters(const WalkArgs &a, unsigned long 
     atomicAdd(&red[5], (unsigned long long)v.sprims);
     atomicAdd(&red[6], (unsigned long long)v.nprims);
     __syncthreads();
-    if (threadIdx.x < 7) atomicAdd(a.stat + threadIdx.x, red[threadIdx.x]);
+    if (threadIdx.x < 7) atomicAdd(stat + threadIdx.x, red[threadIdx.x]);
 }
 
 }  // namespace wost

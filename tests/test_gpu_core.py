@@ -429,3 +429,46 @@ def test_online_training_runs_and_stays_unbiased(api):
     assert np.mean(np.abs(z) < 4.5) > 0.98
     p = F.get_params()
     assert np.all(np.isfinite(p["W1"])) and np.all(np.isfinite(p["grid"]))
+
+
+def test_guided_walks_stay_inside_star(api):
+    # A walker that rounding leaves a hair outside a Neumann segment next to
+    # a reflex vertex must not take the neighbouring segment's entry
+    # crossing as a hit (which flips its side and lets it wander off, where
+    # the decoded mixture is meaningless): walks cast exit-only rays.
+    # Uniform directions through the guided kernel (c = 0) reproduced such
+    # escapes as NaN estimates on this scene before exit-only casts.
+    sc, pts = wi.config_star_guided(res=512)
+    S = api.Scene(sc)
+    lo, hi = S.bbox()
+    F = api.Field(2, lo, hi, seed=1)
+    pd = torch.tensor(pts, dtype=torch.float64, device="cuda")
+    for kw in (dict(c_mode=1, c_fixed=0.0), dict()):
+        m, v, st = api.solve(S, pd, 8, eps=1e-3, maxsteps=128, guided=True, field=F, seed=7, **kw)
+        assert np.all(np.isfinite(m.cpu().numpy())), kw
+    mp, _, _ = api.solve(S, pd, 8, eps=1e-3, maxsteps=128, seed=7)
+    mg, _, _ = api.solve(S, pd, 8, eps=1e-3, maxsteps=128, guided=True, field=F, seed=7, c_mode=1, c_fixed=0.0)
+    assert np.allclose(mg.cpu().numpy(), mp.cpu().numpy(), rtol=1e-6, atol=1e-7)
+    # every recorded walk position lies inside the boundary
+    m, v, st = api.solve(S, pd, 1, eps=1e-3, maxsteps=128, guided=True, field=F, seed=8, c_mode=1, c_fixed=0.0,
+                         train=1, walk_begin=3)
+    rec = F.get_records()
+    assert len(rec) > 1000 and np.all(np.isfinite(rec))
+    x = rec[:, :2].astype(np.float64)
+    onN = rec[:, 9] == 1
+    # interior records: inside, up to rounding at the boundary
+    off = x[~onN]
+    out = off[~wi.inside_star_polygon(sc, off)]
+    assert len(out) <= 1e-5 * len(off), len(out)
+    if len(out):
+        assert _seg_dist_all(sc, out).max() < 1e-5, out[:5]
+    # records on the Neumann boundary: on a segment (a few ulps either side)
+    rng = np.random.default_rng(0)
+    onb = x[onN][rng.choice(int(onN.sum()), min(4000, int(onN.sum())), replace=False)]
+    assert _seg_dist_all(sc, onb).max() < 1e-5
+
+
+def _seg_dist_all(sc, pts):
+    a = sc.verts[sc.prims[:, 0]]
+    b = sc.verts[sc.prims[:, 1]]
+    return np.array([_seg_dist(p[None], a, b).min() for p in pts])

@@ -171,6 +171,68 @@ def test_ray_first_hit_3d_vs_winding_march():
     assert np.all(i3 == -1)                  # leaving a convex-ish shell: nothing further
 
 
+def test_exit_ray_2d_vs_marching():
+    # from inside a closed boundary the first crossing is an exit, so the
+    # exit-only cast equals the two-sided one; from outside it skips the
+    # entry and returns where the ray leaves the domain again
+    sc = wi.star_polyline(128, seed=6, neumann_frac=1.0)
+    S = oracle.Scene(sc)
+    rng = np.random.default_rng(14)
+    org = rng.uniform(-0.5, 0.5, (60, 2))
+    th = rng.uniform(0, 2 * np.pi, 60)
+    dirs = np.stack([np.cos(th), np.sin(th)], 1)
+    i2, t2 = S.ray_neumann(org, dirs, 10.0)
+    ie, te = S.ray_neumann(org, dirs, 10.0, exit_only=True)
+    assert np.array_equal(i2, ie) and np.allclose(t2, te, rtol=1e-12, atol=1e-14)
+    far = 2.0 * np.stack([np.cos(th + np.pi), np.sin(th + np.pi)], 1)   # outside, aimed back across
+    i_in, t_in = S.ray_neumann(far, dirs, 10.0)
+    i_out, t_out = S.ray_neumann(far, dirs, 10.0, exit_only=True)
+    ts = np.linspace(0, 4.5, 45001)
+    for o, d, a, b, ia, ib in zip(far, dirs, t_in, t_out, i_in, i_out):
+        inside = wi.inside_polygon_mask(sc, o[None] + ts[:, None] * d[None])
+        enter = ts[np.argmax(inside)]
+        leave = ts[np.argmax(ts > enter) + np.argmin(inside[ts > enter])]
+        assert ia >= 0 and ib >= 0 and ia != ib
+        assert abs(a - enter) <= 2e-4 and abs(b - leave) <= 2e-4
+        n = S.inward_normal(ib)
+        assert np.dot(d, n) < 0 < np.dot(d, S.inward_normal(ia))
+
+
+def test_exit_ray_at_a_vertex():
+    # a walk standing on the bottom edge of the unit square at its corner
+    # (1, 0), heading barely up (inward for the bottom edge, outward for the
+    # right edge), leaves through the right edge at t = 0: the exit cast
+    # returns it, with t within the rounding band, not a point far outside
+    V = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], float)
+    P = np.array([[i, (i + 1) % 4] for i in range(4)], np.int32)
+    sc = wi.Scene("square", 2, V, P, np.array([1, 1, 1, 0], np.uint8), wi.Fn(wi.FN_ZERO))
+    S = oracle.Scene(sc)
+    d = np.array([[1.0, 1e-4]]) / np.hypot(1.0, 1e-4)
+    for x0 in ([1.0, 0.0], [1.0 - 1e-12, 0.0], [1.0 + 1e-12, 0.0]):
+        i, t = S.ray_neumann(np.array([x0]), d, 10.0, skip=0, exit_only=True)
+        assert i[0] == 1 and abs(t[0]) <= 16 * 2 ** -24 * S.scale, (x0, i, t)
+    # an inward direction for both edges stays in and exits the top edge
+    i, t = S.ray_neumann(np.array([[1.0, 0.0]]), np.array([[-0.6, 0.8]]), 10.0, skip=0, exit_only=True)
+    assert i[0] == 2 and abs(t[0] - 1.25) < 1e-12
+
+
+def test_exit_ray_3d_vs_winding_march():
+    sc = wi.displaced_icosphere(subdiv=1, seed=8, neumann_frac=1.0, with_source=False)
+    S = oracle.Scene(sc)
+    rng = np.random.default_rng(15)
+    dirs = rng.normal(size=(10, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    far = -2.0 * dirs
+    ie, te = S.ray_neumann(far, dirs, 10.0, exit_only=True)
+    for o, d, ti, ii in zip(far, dirs, te, ie):
+        ts = np.linspace(0, 4, 4001)
+        w = S.winding(o[None] + ts[:, None] * d[None]) > 0.5
+        enter = np.argmax(w)
+        leave = ts[enter + np.argmin(w[enter:])]
+        assert ii >= 0 and abs(ti - leave) <= 3e-3
+        assert np.dot(d, S.inward_normal(ii)) < 0
+
+
 def test_winding_vs_crossing_number():
     sc = wi.star_polyline(200, seed=9)
     S = oracle.Scene(sc)

@@ -403,6 +403,55 @@ def config_star_guided(res: int = 512, nseg: int = 4096, seed: int = 2):
     return sc, pts
 
 
+def star_interior_points(sc: Scene, n: int, seed: int) -> np.ndarray:
+    """n seeded points uniform in the interior of a star polygon (rejection
+    from its bounding box)."""
+    rng = np.random.default_rng(seed)
+    lo, hi = sc.bbox
+    out = []
+    have = 0
+    while have < n:
+        cand = lo + (hi - lo) * rng.uniform(0, 1, (max(2 * (n - have), 64), 2))
+        cand = cand[inside_star_polygon(sc, cand)]
+        out.append(cand)
+        have += len(cand)
+    return np.concatenate(out, 0)[:n] if n > 0 else np.zeros((0, 2))
+
+
+@dataclasses.dataclass
+class BatchJob:
+    scene: Scene
+    points: np.ndarray
+    nwalks: int
+    seed: int = 1
+
+
+def _log_uniform_int(rng, lo, hi):
+    return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+
+def config_batch(njobs: int = 64, seed: int = 4, seg_range=(256, 16384), neumann_range=(0.2, 0.5),
+                 points_range=(1024, 262144), wpp_range=(8, 128)):
+    """Many independent 2D problems of uneven size: njobs seeded star
+    polylines (as star_polyline) with log-uniform segment counts in
+    seg_range and a Neumann fraction uniform in neumann_range; each job has a
+    log-uniform number of interior query points in points_range and a
+    log-uniform walk count in wpp_range.  Job j has scene_id j + 1 and walk
+    seed 1000 * seed + j."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for j in range(njobs):
+        nseg = _log_uniform_int(rng, *seg_range)
+        nf = float(rng.uniform(*neumann_range))
+        npts = _log_uniform_int(rng, *points_range)
+        wpp = _log_uniform_int(rng, *wpp_range)
+        sc = star_polyline(nseg, seed=100000 * seed + j, neumann_frac=nf)
+        sc.scene_id = j + 1
+        pts = star_interior_points(sc, npts, seed=200000 * seed + j)
+        jobs.append(BatchJob(sc, pts, wpp, seed=1000 * seed + j))
+    return jobs
+
+
 def subsample(pts: np.ndarray, n: int, seed: int = 0) -> np.ndarray:
     if n >= len(pts):
         return pts
