@@ -116,6 +116,14 @@ typedef struct {
     int64_t max_train_records; /* record buffer capacity (0 = default) */
     int32_t walk_begin;        /* index of the first walk (RNG counter) */
     int32_t ctas_per_sm;       /* launch shape override (0 = default) */
+    int32_t guided_kernel;     /* single-scene guided walks: 0 automatic (the warp-specialised
+                                  kernel for launches that record training data, the wavefront for
+                                  the others), 1 warp-specialised persistent kernel (decode tiles
+                                  served inside the walk kernel), 2 wavefront (step and tcgen05
+                                  decode kernels alternating over walk slots in global memory);
+                                  all draw the same random numbers */
+    int32_t wavefront_slots;   /* walks in flight in a wavefront launch that trains nothing
+                                  (0 = 2^20); a launch that trains holds one walk per point */
 } wost_exec;
 
 typedef struct {

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwost.so")
-SOURCES = ["scene.cu", "walk.cu", "guided.cu", "batch.cu", "train.cu", "capi.cu", "diag.cu", "noalloc.cu"]
+SOURCES = ["scene.cu", "walk.cu", "guided.cu", "wavefront.cu", "batch.cu", "train.cu", "capi.cu", "diag.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC"]
 

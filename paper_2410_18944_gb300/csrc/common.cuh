@@ -96,11 +96,12 @@ __device__ __forceinline__ float eval_fn(const DevFn &fn, const float *x) {
 // n0/n1 are inward unit normals of the two adjacent Neumann primitives.
 // ---------------------------------------------------------------------------
 struct DevBVH {
-    const float4 *nodes;
+    const float4 *nodes;  // global memory, or shared memory when a kernel staged them
     const float4 *prims;
     const int *ids;       // original primitive / element id per leaf slot
     const double *prims64; // FP64 copy of the primitive vertices (leaf order), 2D: 4, 3D: 9 doubles
     int nprims;
+    int nnodes;
 };
 
 struct DevScene {
@@ -113,6 +114,10 @@ struct DevScene {
     DevFn g, f;
     int has_source;
 };
+
+// node and normal-cone loads: generic, as the arrays may have been staged in
+// shared memory by the kernel
+__device__ __forceinline__ float4 ldn(const float4 *p) { return *p; }
 
 __device__ __forceinline__ int leaf_start(int ref) { return (~ref) >> 4; }
 __device__ __forceinline__ int leaf_count(int ref) { return ((~ref) & 15) + 1; }
@@ -127,6 +132,17 @@ __device__ __forceinline__ unsigned long long warp_fetch_add(unsigned long long 
     if (vote && lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(vote));
     base = __shfl_sync(mask, base, leader < 0 ? 0 : leader);
     return base + __popc(vote & ((1u << lane) - 1u));
+}
+
+// warp-aggregated append to a 32-bit counter: returns this lane's slot
+__device__ __forceinline__ unsigned warp_append(unsigned *ctr) {
+    unsigned mask = __activemask();
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(ctr, (unsigned)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
 }
 
 }  // namespace wost

@@ -198,6 +198,46 @@ __device__ __forceinline__ bool mlp_tile_forward(TileCtx &t, const DevField &f, 
     return true;
 }
 
+// shared setup of a 256-thread CTA running two MLP tiles: weight image,
+// two X and two H tiles, two mbarriers, the TMEM base address
+constexpr int kCtaTilesSmem = kWImgBytes + 2 * (128 * kFeat * 2) + 2 * (128 * kHid * 2) + 64;
+
+struct CtaTiles {
+    uint8_t *wimg, *xt, *ht;
+    uint64_t *mbar;
+    uint32_t *tptr;
+};
+
+__device__ __forceinline__ CtaTiles cta_tiles_setup(uint8_t *sm, const DevField &f) {
+    CtaTiles c;
+    c.wimg = sm;
+    c.xt = sm + kWImgBytes;
+    c.ht = c.xt + 2 * (128 * kFeat * 2);
+    c.mbar = reinterpret_cast<uint64_t *>(c.ht + 2 * (128 * kHid * 2));
+    c.tptr = reinterpret_cast<uint32_t *>(c.mbar + 2);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kWImgBytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(c.wimg)[i] = __ldg(f.wimg + i);
+    if (tid == 0) {
+        mbar_init(&c.mbar[0], 1);
+        mbar_init(&c.mbar[1], 1);
+        fence_mbar_init();
+    }
+    if (tid < 32) tmem_alloc(c.tptr, 128);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return c;
+}
+
+__device__ __forceinline__ void cta_tiles_teardown(const CtaTiles &c) {
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(*c.tptr, 128);
+}
+
 }  // namespace wost
 
 // host-side field state

@@ -22,10 +22,10 @@ template <> struct NodeFloats<3> { static constexpr int n = 4; };
 
 // squared distance from x to the two child boxes of a node
 template <int D>
-__device__ __forceinline__ void node_box_d2(const float4 *__restrict__ nodes, int node, const float *x,
+__device__ __forceinline__ void node_box_d2(const float4 *nodes, int node, const float *x,
                                             float &d0, float &d1, int &r0, int &r1) {
     if (D == 2) {
-        const float4 a = __ldg(nodes + 3 * node), b = __ldg(nodes + 3 * node + 1), r = __ldg(nodes + 3 * node + 2);
+        const float4 a = ldn(nodes + 3 * node), b = ldn(nodes + 3 * node + 1), r = ldn(nodes + 3 * node + 2);
         float ax = fmaxf(fmaxf(a.x - x[0], x[0] - a.z), 0.f), ay = fmaxf(fmaxf(a.y - x[1], x[1] - a.w), 0.f);
         float bx = fmaxf(fmaxf(b.x - x[0], x[0] - b.z), 0.f), by = fmaxf(fmaxf(b.y - x[1], x[1] - b.w), 0.f);
         d0 = ax * ax + ay * ay;
@@ -33,8 +33,8 @@ __device__ __forceinline__ void node_box_d2(const float4 *__restrict__ nodes, in
         r0 = __float_as_int(r.x);
         r1 = __float_as_int(r.y);
     } else {
-        const float4 a = __ldg(nodes + 4 * node), b = __ldg(nodes + 4 * node + 1);
-        const float4 c = __ldg(nodes + 4 * node + 2), r = __ldg(nodes + 4 * node + 3);
+        const float4 a = ldn(nodes + 4 * node), b = ldn(nodes + 4 * node + 1);
+        const float4 c = ldn(nodes + 4 * node + 2), r = ldn(nodes + 4 * node + 3);
         // child 0: lo = (a.x, a.y, a.z) hi = (a.w, b.x, b.y); child 1: lo = (b.z, b.w, c.x) hi = (c.y, c.z, c.w)
         float ax = fmaxf(fmaxf(a.x - x[0], x[0] - a.w), 0.f);
         float ay = fmaxf(fmaxf(a.y - x[1], x[1] - b.x), 0.f);
@@ -53,19 +53,19 @@ __device__ __forceinline__ void node_box_d2(const float4 *__restrict__ nodes, in
 // (exit casts: from t > -pad, boxes grown by pad on every side, so that
 // crossings within the rounding band of a primitive are not pruned)
 template <int D>
-__device__ __forceinline__ void node_box_ray(const float4 *__restrict__ nodes, int node, const float *o,
+__device__ __forceinline__ void node_box_ray(const float4 *nodes, int node, const float *o,
                                              const float *inv, float tmax, float &t0, float &t1,
                                              int &r0, int &r1, float pad = 0.f) {
     float lo0[3], hi0[3], lo1[3], hi1[3];
     if (D == 2) {
-        const float4 a = __ldg(nodes + 3 * node), b = __ldg(nodes + 3 * node + 1), r = __ldg(nodes + 3 * node + 2);
+        const float4 a = ldn(nodes + 3 * node), b = ldn(nodes + 3 * node + 1), r = ldn(nodes + 3 * node + 2);
         lo0[0] = a.x; lo0[1] = a.y; hi0[0] = a.z; hi0[1] = a.w;
         lo1[0] = b.x; lo1[1] = b.y; hi1[0] = b.z; hi1[1] = b.w;
         r0 = __float_as_int(r.x);
         r1 = __float_as_int(r.y);
     } else {
-        const float4 a = __ldg(nodes + 4 * node), b = __ldg(nodes + 4 * node + 1);
-        const float4 c = __ldg(nodes + 4 * node + 2), r = __ldg(nodes + 4 * node + 3);
+        const float4 a = ldn(nodes + 4 * node), b = ldn(nodes + 4 * node + 1);
+        const float4 c = ldn(nodes + 4 * node + 2), r = ldn(nodes + 4 * node + 3);
         lo0[0] = a.x; lo0[1] = a.y; lo0[2] = a.z; hi0[0] = a.w; hi0[1] = b.x; hi0[2] = b.y;
         lo1[0] = b.z; lo1[1] = b.w; lo1[2] = c.x; hi1[0] = c.y; hi1[1] = c.z; hi1[2] = c.w;
         r0 = __float_as_int(r.x);
@@ -284,14 +284,14 @@ __device__ __forceinline__ bool cone_prunes(float4 cone, const float *lo, const 
 }
 
 template <int D>
-__device__ __forceinline__ void child_boxes(const float4 *__restrict__ nodes, int node, float *lo0, float *hi0,
+__device__ __forceinline__ void child_boxes(const float4 *nodes, int node, float *lo0, float *hi0,
                                             float *lo1, float *hi1) {
     if (D == 2) {
-        const float4 a = __ldg(nodes + 3 * node), b = __ldg(nodes + 3 * node + 1);
+        const float4 a = ldn(nodes + 3 * node), b = ldn(nodes + 3 * node + 1);
         lo0[0] = a.x; lo0[1] = a.y; hi0[0] = a.z; hi0[1] = a.w;
         lo1[0] = b.x; lo1[1] = b.y; hi1[0] = b.z; hi1[1] = b.w;
     } else {
-        const float4 a = __ldg(nodes + 4 * node), b = __ldg(nodes + 4 * node + 1), c = __ldg(nodes + 4 * node + 2);
+        const float4 a = ldn(nodes + 4 * node), b = ldn(nodes + 4 * node + 1), c = ldn(nodes + 4 * node + 2);
         lo0[0] = a.x; lo0[1] = a.y; lo0[2] = a.z; hi0[0] = a.w; hi0[1] = b.x; hi0[2] = b.y;
         lo1[0] = b.z; lo1[1] = b.w; lo1[2] = c.x; hi1[0] = c.y; hi1[1] = c.z; hi1[2] = c.w;
     }
@@ -321,8 +321,8 @@ __device__ int closest_silhouette(const DevBVH &bv, const float *x, float tau, f
             if (cones && (h0 || h1)) {
                 float lo0[3], hi0[3], lo1[3], hi1[3];
                 child_boxes<D>(bv.nodes, ref, lo0, hi0, lo1, hi1);
-                if (h0 && cone_prunes<D>(__ldg(cones + 2 * ref), lo0, hi0, x, d0, tau)) h0 = false;
-                if (h1 && cone_prunes<D>(__ldg(cones + 2 * ref + 1), lo1, hi1, x, d1, tau)) h1 = false;
+                if (h0 && cone_prunes<D>(ldn(cones + 2 * ref), lo0, hi0, x, d0, tau)) h0 = false;
+                if (h1 && cone_prunes<D>(ldn(cones + 2 * ref + 1), lo1, hi1, x, d1, tau)) h1 = false;
             }
             if (h0 && h1) {
                 bool first0 = d0 <= d1;

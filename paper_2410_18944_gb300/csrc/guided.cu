@@ -10,7 +10,7 @@
 namespace wost {
 
 constexpr int kGuidedBlock = 256;
-constexpr int kGuidedSmem = kWImgBytes + 2 * kXTileBytes + 2 * kHTileBytes + 64;
+constexpr int kGuidedSmem = kCtaTilesSmem;
 constexpr int kWsSmem = ws_smem_bytes(false);
 
 struct GuidedArgs {
@@ -18,49 +18,19 @@ struct GuidedArgs {
     DevField f;
     WsOpts o;
     RecDest rd;
+    int stage_f4;      // float4 of BVH nodes / cones staged in shared memory (0: none)
 };
-
-// shared setup of a 256-thread CTA running two MLP tiles
-struct CtaTiles {
-    uint8_t *wimg, *xt, *ht;
-    uint64_t *mbar;
-    uint32_t *tptr;
-};
-
-__device__ __forceinline__ CtaTiles cta_tiles_setup(uint8_t *sm, const DevField &f) {
-    CtaTiles c;
-    c.wimg = sm;
-    c.xt = sm + kWImgBytes;
-    c.ht = c.xt + 2 * kXTileBytes;
-    c.mbar = reinterpret_cast<uint64_t *>(c.ht + 2 * kHTileBytes);
-    c.tptr = reinterpret_cast<uint32_t *>(c.mbar + 2);
-    const int tid = threadIdx.x;
-    for (int i = tid; i < kWImgBytes / 16; i += blockDim.x)
-        reinterpret_cast<uint4 *>(c.wimg)[i] = __ldg(f.wimg + i);
-    if (tid == 0) {
-        mbar_init(&c.mbar[0], 1);
-        mbar_init(&c.mbar[1], 1);
-        fence_mbar_init();
-    }
-    if (tid < 32) tmem_alloc(c.tptr, 128);
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    return c;
-}
-
-__device__ __forceinline__ void cta_tiles_teardown(const CtaTiles &c) {
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (threadIdx.x < 32) tmem_dealloc(*c.tptr, 128);
-}
 
 template <int D>
 __global__ void __launch_bounds__(kWsThreads, 1) guided_walk_kernel(const __grid_constant__ GuidedArgs g) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    guided_ws_body<D, false>(SoloSrc<D>{g.w, &g.f, g.rd}, g.o, sm);
+    __shared__ DevScene staged;
+    const DevScene *sc = &g.w.sc;
+    if (g.stage_f4 > 0) {
+        stage_scene(g.w.sc, staged, reinterpret_cast<float4 *>(sm + kWsSmem));
+        sc = &staged;
+    }
+    guided_ws_body<D, false>(SoloSrc<D>{g.w, &g.f, g.rd, sc}, g.o, sm);
 }
 
 // decode of arbitrary points: the same tile forward as inside the walk
@@ -132,32 +102,50 @@ wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_ada
 
 int guided_ctas_per_sm() { return 1; }
 
-// the warp-specialised walk kernel runs one CTA (640 threads) per SM
+// the warp-specialised walk kernel runs one CTA (512 threads) per SM; its
+// dynamic shared memory holds the decode tiles and, when they fit, the
+// scene's BVH nodes and cones
+constexpr int kStageMaxBytes = 96 * 1024;
+
 wost_status guided_occupancy(int dim, int *per_sm) {
     static bool set[4] = {false, false, false, false};
     if (!set[dim]) {
-        if (dim == 2) WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmem));
-        else WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWsSmem));
+        const int bytes = kWsSmem + kStageMaxBytes;
+        if (dim == 2) WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        else WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         set[dim] = true;
     }
     *per_sm = 1;
     return WOST_OK;
 }
 
+int stage_f4_for(const DevScene &sc) {
+    const int f4 = scene_node_f4(sc);
+    return f4 * 16 <= kStageMaxBytes ? f4 : 0;
+}
+
 wost_status launch_guided(int dim, const GuidedArgs &g, int grid, cudaStream_t st) {
-    if (dim == 2) guided_walk_kernel<2><<<grid, kWsThreads, kWsSmem, st>>>(g);
-    else guided_walk_kernel<3><<<grid, kWsThreads, kWsSmem, st>>>(g);
+    const int smem = kWsSmem + g.stage_f4 * 16;
+    if (dim == 2) guided_walk_kernel<2><<<grid, kWsThreads, smem, st>>>(g);
+    else guided_walk_kernel<3><<<grid, kWsThreads, smem, st>>>(g);
     WOST_CUDA(cudaGetLastError());
     return WOST_OK;
 }
 
 wost_status ensure_records(wost_field *f, int64_t cap, size_t scratch_bytes);
+wost_status wavefront_run(wost_scene *sc, wost_field *f, const WalkArgs &a, const WsOpts &o, const RecDest &rd,
+                          int max_slots, cudaStream_t st, int64_t *iters_out);
+
+// walk slots of a wavefront launch that trains nothing (walks beyond the slots
+// queue up behind them)
+constexpr int kWfMaxSlots = 1 << 20;
 
 wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, const wost_exec &ex,
                          cudaStream_t st, wost_stats *stats, int walk_begin, CallTiming &tm) {
     if (f->desc.dim != s->dim) { set_error("wost_solve: field dimension differs from the scene"); return WOST_ERR_INVALID_ARG; }
     GuidedArgs g{};
     g.f = f->dev();
+    g.stage_f4 = stage_f4_for(s->dev);
     g.o.c_mode = ex.c_mode;
     g.o.c_fixed = ex.c_fixed;
     g.o.reflect = ex.reflect;
@@ -167,43 +155,96 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
     f->t_c_mode = ex.c_mode;
     f->t_c_fixed = ex.c_fixed;
     f->t_reflect = ex.reflect;
-    int occ = 1;
-    wost_status orc = guided_occupancy(s->dim, &occ);
-    if (orc != WOST_OK) return orc;
-    int cps = ex.ctas_per_sm > 0 ? std::min(ex.ctas_per_sm, occ) : occ;
-    int grid = num_sms() * cps;
-    const bool any_train = ex.train && walk_begin < ex.train_until_wpp;
-    if (any_train) {
-        int64_t cap = ex.max_train_records > 0 ? ex.max_train_records : std::max<int64_t>(a.npoints * 64, 1 << 20);
-        size_t scratch = (size_t)grid * (kWsWalkerWarps * 32) * (size_t)std::max(a.maxsteps, 1) * kRecFloats * sizeof(float);
-        wost_status rc = ensure_records(f, cap, scratch);
-        if (rc != WOST_OK) return rc;
-    }
-    g.o.scratch = f->scratch;
-    g.o.scratch_steps = a.maxsteps;
-    g.rd = RecDest{f->rec, f->rec_ctr, f->rec_cap};
+    // Launch selection.  A launch that records training data holds one walk
+    // per point (the field trains after it), and its time is set by how fast
+    // walkers finish a few walks each: the asynchronous warp-specialised
+    // kernel serves that best.  Launches without records run every walk at
+    // once, and the wavefront keeps its slots full of them.
+    const int rounds = ex.train ? std::max(0, std::min(nwalks, ex.train_until_wpp - walk_begin)) : 0;
+    const bool wavefront = ex.guided_kernel == 2 || (ex.guided_kernel == 0 && rounds == 0);
+    const bool ws_then_wavefront = ex.guided_kernel == 0 && rounds > 0 && rounds < nwalks;
     int ntrain = 0;
-    for (int b = 0; b < nwalks; ++b) {
-        g.w = a;
-        g.w.walk_begin = walk_begin + b;
-        g.w.total = (unsigned long long)a.npoints;
-        g.o.record = ex.train && (walk_begin + b) < ex.train_until_wpp;
+    // one wavefront launch of `items` walks from walk index w0
+    auto run_wavefront = [&](int w0, unsigned long long items, bool record) -> wost_status {
+        WalkArgs w = a;
+        w.walk_begin = w0;
+        w.total = items;
+        g.o.record = record;
         WOST_CUDA(cudaMemsetAsync(a.work_ctr, 0, sizeof(unsigned long long), st));
-        if (g.o.record) WOST_CUDA(cudaMemsetAsync(f->rec_ctr, 0, 2 * sizeof(unsigned long long), st));
-        g.f = f->dev();
+        if (record) WOST_CUDA(cudaMemsetAsync(f->rec_ctr, 0, 2 * sizeof(unsigned long long), st));
+        int64_t iters = 0;
+        const int slots = record ? (int)a.npoints : (ex.wavefront_slots > 0 ? ex.wavefront_slots : kWfMaxSlots);
         tm.mark(tm.walk, st);
-        wost_status rc = launch_guided(s->dim, g, grid, st);
+        wost_status rc = wavefront_run(s, f, w, g.o, g.rd, slots, st, &iters);
         tm.mark(tm.walk, st);
-        tm.launches++;
-        tm.walk_launches++;
-        if (rc != WOST_OK) return rc;
-        if (g.o.record) {
-            tm.mark(tm.train, st);
-            rc = train_launch(f, s->dim, st, true, nullptr);
-            tm.mark(tm.train, st);
-            tm.launches += 5;   // gradient, Adam step count, Adam, FP16 grid copy, BF16 weight image
+        tm.launches += 2 * iters;
+        tm.walk_launches += 2 * iters;
+        return rc;
+    };
+    auto train_after = [&]() -> wost_status {
+        tm.mark(tm.train, st);
+        wost_status rc = train_launch(f, s->dim, st, true, nullptr);
+        tm.mark(tm.train, st);
+        tm.launches += 5;   // gradient, Adam step count, Adam, FP16 grid copy, BF16 weight image
+        ntrain++;
+        return rc;
+    };
+    g.rd = RecDest{f->rec, f->rec_ctr, f->rec_cap};
+    g.o.scratch_steps = a.maxsteps;
+    if (wavefront) {
+        // one launch of npoints walks per training round, then every
+        // remaining walk in one launch (the random numbers of a walk do not
+        // depend on how walks are grouped into launches)
+        if (rounds > 0) {
+            int64_t cap = ex.max_train_records > 0 ? ex.max_train_records : std::max<int64_t>(a.npoints * 64, 1 << 20);
+            size_t scratch = (size_t)a.npoints * (size_t)std::max(a.maxsteps, 1) * kRecFloats * sizeof(float);
+            wost_status rc = ensure_records(f, cap, scratch);
             if (rc != WOST_OK) return rc;
-            ntrain++;
+            g.rd = RecDest{f->rec, f->rec_ctr, f->rec_cap};
+        }
+        g.o.scratch = f->scratch;
+        for (int b = 0; b < rounds; ++b) {
+            wost_status rc = run_wavefront(walk_begin + b, (unsigned long long)a.npoints, true);
+            if (rc == WOST_OK) rc = train_after();
+            if (rc != WOST_OK) return rc;
+        }
+        if (rounds < nwalks) {
+            wost_status rc = run_wavefront(walk_begin + rounds, (unsigned long long)a.npoints * (nwalks - rounds), false);
+            if (rc != WOST_OK) return rc;
+        }
+    } else {
+        int occ = 1;
+        wost_status orc = guided_occupancy(s->dim, &occ);
+        if (orc != WOST_OK) return orc;
+        int cps = ex.ctas_per_sm > 0 ? std::min(ex.ctas_per_sm, occ) : occ;
+        int grid = num_sms() * cps;
+        if (rounds > 0) {
+            int64_t cap = ex.max_train_records > 0 ? ex.max_train_records : std::max<int64_t>(a.npoints * 64, 1 << 20);
+            size_t scratch = (size_t)grid * (kWsWalkerWarps * 32) * (size_t)std::max(a.maxsteps, 1) * kRecFloats * sizeof(float);
+            wost_status rc = ensure_records(f, cap, scratch);
+            if (rc != WOST_OK) return rc;
+            g.rd = RecDest{f->rec, f->rec_ctr, f->rec_cap};
+        }
+        g.o.scratch = f->scratch;
+        const int ws_walks = ws_then_wavefront ? rounds : nwalks;
+        for (int b = 0; b < ws_walks; ++b) {
+            g.w = a;
+            g.w.walk_begin = walk_begin + b;
+            g.w.total = (unsigned long long)a.npoints;
+            g.o.record = b < rounds;
+            WOST_CUDA(cudaMemsetAsync(a.work_ctr, 0, sizeof(unsigned long long), st));
+            if (g.o.record) WOST_CUDA(cudaMemsetAsync(f->rec_ctr, 0, 2 * sizeof(unsigned long long), st));
+            tm.mark(tm.walk, st);
+            wost_status rc = launch_guided(s->dim, g, grid, st);
+            tm.mark(tm.walk, st);
+            tm.launches++;
+            tm.walk_launches++;
+            if (rc != WOST_OK) return rc;
+            if (g.o.record && (rc = train_after()) != WOST_OK) return rc;
+        }
+        if (ws_then_wavefront) {
+            wost_status rc = run_wavefront(walk_begin + rounds, (unsigned long long)a.npoints * (nwalks - rounds), false);
+            if (rc != WOST_OK) return rc;
         }
     }
     if (stats) {

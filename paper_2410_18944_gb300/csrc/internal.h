@@ -44,6 +44,8 @@ struct wost_scene {
     int depth_dir = 0, depth_neu = 0, depth_sil = 0;
     // per-solve workspace (grown on demand)
     wost::DevBuf ws_points, ws_status, ws_sum, ws_sum2, ws_ctr, ws_out;
+    wost::DevBuf ws_wf;                        // guided wavefront slots
+    unsigned long long *pinned = nullptr;      // host-pinned words for wavefront progress
     ~wost_scene();
 };
 

@@ -36,6 +36,7 @@ struct SoloSrc {
     const WalkArgs &a;
     const DevField *f;   // guided only
     RecDest rd;
+    const DevScene *sc;  // the scene view the steps use (a.sc, or a copy on staged nodes)
 
     __device__ __forceinline__ unsigned long long *work_ctr() const { return a.work_ctr; }
     __device__ __forceinline__ unsigned long long total() const { return a.total; }
@@ -43,7 +44,9 @@ struct SoloSrc {
         start_walk<D>(w, a, item);
         return a.status[w.pid] == 0;
     }
-    __device__ __forceinline__ StepEnv env(const Walk<D> &) const { return env_of(a); }
+    __device__ __forceinline__ StepEnv env(const Walk<D> &) const {
+        return StepEnv{*sc, a.eps, a.eps64, a.maxsteps, a.key0, a.key1, a.err};
+    }
     __device__ __forceinline__ void finish(const Walk<D> &w) const { finish_walk(a, w.pid, w.acc); }
     __device__ __forceinline__ const DevField &field(const Walk<D> &) const { return *f; }
     __device__ __forceinline__ RecDest rec(const Walk<D> &) const { return rd; }
@@ -51,6 +54,40 @@ struct SoloSrc {
     __device__ __forceinline__ const uint4 *wimg(int) const { return f->wimg; }
     __device__ __forceinline__ const float *b3(int) const { return f->b3; }
 };
+
+// Float4 count of a scene's BVH nodes and silhouette normal cones, the data
+// every traversal step reads first.
+__host__ __device__ __forceinline__ int scene_node_f4(const DevScene &s) {
+    const int nb = s.dim == 2 ? 3 : 4;
+    return (s.dir.nnodes + s.neu.nnodes + s.sil.nnodes) * nb + (s.sil_cones ? 2 * s.sil.nnodes : 0);
+}
+
+// Copies the BVH nodes and cones of `in` into shared memory `dst` (all
+// threads of the block take part) and makes `out` (shared) a copy of the
+// scene view pointing at them.  Traversal node loads then come from shared
+// memory: a walk step is a chain of dependent node loads, so their latency
+// is the step's latency.
+__device__ __forceinline__ void stage_scene(const DevScene &in, DevScene &out, float4 *dst) {
+    const int nb = in.dim == 2 ? 3 : 4;
+    const float4 *src[4] = {in.dir.nodes, in.neu.nodes, in.sil.nodes, in.sil_cones};
+    const int cnt[4] = {in.dir.nnodes * nb, in.neu.nnodes * nb, in.sil.nnodes * nb, in.sil_cones ? 2 * in.sil.nnodes : 0};
+    float4 *start[4];
+    float4 *d = dst;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        start[r] = d;
+        for (int i = threadIdx.x; i < cnt[r]; i += blockDim.x) d[i] = __ldg(src[r] + i);
+        d += cnt[r];
+    }
+    if (threadIdx.x == 0) {
+        out = in;
+        if (cnt[0]) out.dir.nodes = start[0];
+        if (cnt[1]) out.neu.nodes = start[1];
+        if (cnt[2]) out.sil.nodes = start[2];
+        if (cnt[3]) out.sil_cones = start[3];
+    }
+    __syncthreads();
+}
 
 // ---------------------------------------------------------------------------
 // many scenes

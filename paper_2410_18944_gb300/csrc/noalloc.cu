@@ -85,7 +85,7 @@ __global__ void static_classify_kernel(WalkArgs a, double *shell_value) {
 // the plain persistent walk loop, on the static scratch
 template <int D>
 __global__ void __launch_bounds__(128) static_walk_kernel(const __grid_constant__ WalkArgs a) {
-    plain_loop<D>(SoloSrc<D>{a, nullptr, RecDest{}}, a.stat);
+    plain_loop<D>(SoloSrc<D>{a, nullptr, RecDest{}, &a.sc}, a.stat);
 }
 
 __global__ void static_finalize_kernel(const uint8_t *status, const double *shell_value, const double *sum,

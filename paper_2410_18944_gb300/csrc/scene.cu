@@ -251,6 +251,8 @@ using namespace wost;
 wost_scene::~wost_scene() {
     for (void *p : allocs) cudaFree(p);
     ws_points.release(); ws_status.release(); ws_sum.release(); ws_sum2.release(); ws_ctr.release(); ws_out.release();
+    ws_wf.release();
+    if (pinned) cudaFreeHost(pinned);
 }
 
 extern "C" wost_status wost_create_scene(const wost_scene_desc *desc, wost_scene **out) {
@@ -359,6 +361,7 @@ extern "C" wost_status wost_create_scene(const wost_scene_desc *desc, wost_scene
         }
         wost_status st;
         if ((st = upload(s, B.pack(), &bv.nodes)) != WOST_OK) return st;
+        bv.nnodes = (int)B.nodes.size();
         if ((st = upload(s, prims, &bv.prims)) != WOST_OK) return st;
         if ((st = upload(s, ids, &bv.ids)) != WOST_OK) return st;
         if ((st = upload(s, p64, &bv.prims64)) != WOST_OK) return st;
@@ -461,6 +464,7 @@ extern "C" wost_status wost_create_scene(const wost_scene_desc *desc, wost_scene
             delete s;
             return st;
         }
+        bv.nnodes = (int)B.nodes.size();
         const int64_t *kp = nullptr;
         if ((st = upload(s, keys, &kp)) != WOST_OK) { delete s; return st; }
         s->sil_key = const_cast<int64_t *>(kp);

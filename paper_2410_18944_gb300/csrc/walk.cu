@@ -68,7 +68,7 @@ constexpr int kPlainBlock = 128;
 
 template <int D>
 __global__ void __launch_bounds__(kPlainBlock) plain_walk_kernel(const __grid_constant__ WalkArgs a) {
-    plain_loop<D>(SoloSrc<D>{a, nullptr, RecDest{}}, a.stat);
+    plain_loop<D>(SoloSrc<D>{a, nullptr, RecDest{}, &a.sc}, a.stat);
 }
 
 // status of every query point: 2 outside (odd/even crossing count of a ray

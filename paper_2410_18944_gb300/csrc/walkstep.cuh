@@ -266,7 +266,7 @@ __device__ __forceinline__ void flush_stats(unsigned long long *stat, unsigned l
     atomicAdd(&red[5], (unsigned long long)v.sprims);
     atomicAdd(&red[6], (unsigned long long)v.nprims);
     __syncthreads();
-    if (threadIdx.x < 7) atomicAdd(stat + threadIdx.x, red[threadIdx.x]);
+    if (threadIdx.x < 7 && red[threadIdx.x]) atomicAdd(stat + threadIdx.x, red[threadIdx.x]);
 }
 
 }  // namespace wost

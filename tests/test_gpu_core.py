@@ -472,3 +472,26 @@ def _seg_dist_all(sc, pts):
     a = sc.verts[sc.prims[:, 0]]
     b = sc.verts[sc.prims[:, 1]]
     return np.array([_seg_dist(p[None], a, b).min() for p in pts])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_wavefront_equals_warp_specialised(api, dim):
+    # the two guided kernels draw the same random numbers and decode the same
+    # FP16 rows, so with a frozen field their estimates agree up to the order
+    # of the FP64 atomic sums; more walks than slots exercises slot refill,
+    # and the automatic choice runs a frozen solve on the wavefront
+    sc = wi.star_polyline(512, seed=3) if dim == 2 else wi.displaced_icosphere(subdiv=3, seed=4)
+    S = api.Scene(sc)
+    F, _, _ = _field_pair(api, dim, 21, sc, w_scale=1.2)
+    pts = _interior(sc, 300, 13, margin=0.02)
+    pd = torch.tensor(pts, dtype=torch.float64, device="cuda")
+    out = []
+    for kern, slots in ((1, 0), (2, 0), (2, 1000), (0, 0)):
+        m, v, st = api.solve(S, pd, 24, eps=1e-3, maxsteps=256, guided=True, field=F, seed=31, guided_kernel=kern,
+                             wavefront_slots=slots)
+        out.append((m.cpu().numpy(), v.cpu().numpy(), st))
+    m1, v1, s1 = out[0]
+    for m0, v0, s0 in out[1:]:
+        assert s0["walk_steps"] == s1["walk_steps"] and s0["walks"] == s1["walks"]
+        assert np.allclose(m0, m1, rtol=1e-9, atol=1e-12)
+        assert np.allclose(v0, v1, rtol=1e-6, atol=1e-12)
