@@ -177,7 +177,9 @@ wost_status wost_solve(wost_scene *scene, wost_field *field, const double *point
 /* Neural field lifetime and parameters (exchange layout, float32):
    grid [L][2^log2_table][F], W1 [H][L F], W2 [H][H], W3 [nout][H], b3 [nout]
    with nout = (dim + 2) K + 1; output order mu'_i (K x d), kappa'_i (K),
-   lambda'_i (K), c' (Tab. reg_map). */
+   lambda'_i (K), c' (Tab. reg_map).  Parameter and gradient arrays of
+   set_params / get_params / wost_train_grad may be host or device memory
+   (unified addressing); set_params resets the Adam moments and step count. */
 wost_status wost_create_field(const wost_field_desc *desc, wost_field **out);
 wost_status wost_destroy_field(wost_field *field);
 wost_status wost_field_set_params(wost_field *field, const float *grid, const float *W1,
@@ -204,7 +206,9 @@ wost_status wost_train_records(wost_field *field, const float *records, int64_t 
 /* Copies up to cap records of the buffer to host memory; *n = count. */
 wost_status wost_get_records(const wost_field *field, float *records, int64_t cap, int64_t *n);
 /* Loss and gradients without the Adam update: grads in the exchange layout
-   (host), for checking against the FP64 reference. */
+   (host or device; nullable each), from the same fused kernel as
+   wost_train_step: the forward is recomputed from the records and the
+   backward runs on tensor cores (the binding's torch.autograd.Function). */
 wost_status wost_train_grad(wost_field *field, const wost_exec *exec, float *out_loss,
                             float *g_grid, float *g_W1, float *g_W2, float *g_W3, float *g_b3);
 

@@ -211,11 +211,11 @@ extern "C" wost_status wost_field_set_params(wost_field *f, const float *grid, c
     if (!f || !grid || !W1 || !W2 || !W3 || !b3) { set_error("wost_field_set_params: null argument"); return WOST_ERR_INVALID_ARG; }
     const int H = f->desc.hidden, nin = f->desc.levels * f->desc.features;
     float *d = f->mlp32;
-    WOST_CUDA(cudaMemcpy(f->grid32, grid, f->n_grid() * sizeof(float), cudaMemcpyHostToDevice));
-    WOST_CUDA(cudaMemcpy(d, W1, (size_t)H * nin * sizeof(float), cudaMemcpyHostToDevice));
-    WOST_CUDA(cudaMemcpy(d + H * nin, W2, (size_t)H * H * sizeof(float), cudaMemcpyHostToDevice));
-    WOST_CUDA(cudaMemcpy(d + H * nin + H * H, W3, (size_t)f->nout * H * sizeof(float), cudaMemcpyHostToDevice));
-    WOST_CUDA(cudaMemcpy(d + H * nin + H * H + f->nout * H, b3, f->nout * sizeof(float), cudaMemcpyHostToDevice));
+    WOST_CUDA(cudaMemcpy(f->grid32, grid, f->n_grid() * sizeof(float), cudaMemcpyDefault));
+    WOST_CUDA(cudaMemcpy(d, W1, (size_t)H * nin * sizeof(float), cudaMemcpyDefault));
+    WOST_CUDA(cudaMemcpy(d + H * nin, W2, (size_t)H * H * sizeof(float), cudaMemcpyDefault));
+    WOST_CUDA(cudaMemcpy(d + H * nin + H * H, W3, (size_t)f->nout * H * sizeof(float), cudaMemcpyDefault));
+    WOST_CUDA(cudaMemcpy(d + H * nin + H * H + f->nout * H, b3, f->nout * sizeof(float), cudaMemcpyDefault));
     WOST_CUDA(cudaMemset(f->grid_m, 0, f->n_grid() * sizeof(float)));
     WOST_CUDA(cudaMemset(f->grid_v, 0, f->n_grid() * sizeof(float)));
     WOST_CUDA(cudaMemset(f->mlp_m, 0, f->n_mlp() * sizeof(float)));
@@ -233,11 +233,11 @@ extern "C" wost_status wost_field_get_params(const wost_field *f, float *grid, f
     const int H = f->desc.hidden, nin = f->desc.levels * f->desc.features;
     const float *d = f->mlp32;
     WOST_CUDA(cudaDeviceSynchronize());
-    if (grid) WOST_CUDA(cudaMemcpy(grid, f->grid32, f->n_grid() * sizeof(float), cudaMemcpyDeviceToHost));
-    if (W1) WOST_CUDA(cudaMemcpy(W1, d, (size_t)H * nin * sizeof(float), cudaMemcpyDeviceToHost));
-    if (W2) WOST_CUDA(cudaMemcpy(W2, d + H * nin, (size_t)H * H * sizeof(float), cudaMemcpyDeviceToHost));
-    if (W3) WOST_CUDA(cudaMemcpy(W3, d + H * nin + H * H, (size_t)f->nout * H * sizeof(float), cudaMemcpyDeviceToHost));
-    if (b3) WOST_CUDA(cudaMemcpy(b3, d + H * nin + H * H + f->nout * H, f->nout * sizeof(float), cudaMemcpyDeviceToHost));
+    if (grid) WOST_CUDA(cudaMemcpy(grid, f->grid32, f->n_grid() * sizeof(float), cudaMemcpyDefault));
+    if (W1) WOST_CUDA(cudaMemcpy(W1, d, (size_t)H * nin * sizeof(float), cudaMemcpyDefault));
+    if (W2) WOST_CUDA(cudaMemcpy(W2, d + H * nin, (size_t)H * H * sizeof(float), cudaMemcpyDefault));
+    if (W3) WOST_CUDA(cudaMemcpy(W3, d + H * nin + H * H, (size_t)f->nout * H * sizeof(float), cudaMemcpyDefault));
+    if (b3) WOST_CUDA(cudaMemcpy(b3, d + H * nin + H * H + f->nout * H, f->nout * sizeof(float), cudaMemcpyDefault));
     return WOST_OK;
 }
 
@@ -305,10 +305,10 @@ extern "C" wost_status wost_train_grad(wost_field *f, const wost_exec *exec, flo
     if ((rc = device_check(st)) != WOST_OK) return rc;
     const int H = f->desc.hidden, nin = f->desc.levels * f->desc.features;
     const float *d = f->mlp_g;
-    if (g_grid) WOST_CUDA(cudaMemcpy(g_grid, f->grid_g, f->n_grid() * sizeof(float), cudaMemcpyDeviceToHost));
-    if (g_W1) WOST_CUDA(cudaMemcpy(g_W1, d, (size_t)H * nin * sizeof(float), cudaMemcpyDeviceToHost));
-    if (g_W2) WOST_CUDA(cudaMemcpy(g_W2, d + H * nin, (size_t)H * H * sizeof(float), cudaMemcpyDeviceToHost));
-    if (g_W3) WOST_CUDA(cudaMemcpy(g_W3, d + H * nin + H * H, (size_t)f->nout * H * sizeof(float), cudaMemcpyDeviceToHost));
-    if (g_b3) WOST_CUDA(cudaMemcpy(g_b3, d + H * nin + H * H + f->nout * H, f->nout * sizeof(float), cudaMemcpyDeviceToHost));
+    if (g_grid) WOST_CUDA(cudaMemcpy(g_grid, f->grid_g, f->n_grid() * sizeof(float), cudaMemcpyDefault));
+    if (g_W1) WOST_CUDA(cudaMemcpy(g_W1, d, (size_t)H * nin * sizeof(float), cudaMemcpyDefault));
+    if (g_W2) WOST_CUDA(cudaMemcpy(g_W2, d + H * nin, (size_t)H * H * sizeof(float), cudaMemcpyDefault));
+    if (g_W3) WOST_CUDA(cudaMemcpy(g_W3, d + H * nin + H * H, (size_t)f->nout * H * sizeof(float), cudaMemcpyDefault));
+    if (g_b3) WOST_CUDA(cudaMemcpy(g_b3, d + H * nin + H * H + f->nout * H, f->nout * sizeof(float), cudaMemcpyDefault));
     return WOST_OK;
 }
