@@ -365,6 +365,97 @@ def run_ours(args):
     return 0
 
 
+WORKLOADS = {
+    "sphere3d": dict(workload="3D mixed Dirichlet/Neumann Poisson guided WoSt: icosphere 81,920 triangles displaced "
+                              "by 0.15 Perlin noise, 30% Neumann cap, f = 4 Gaussians (sigma 0.1), g = 1/|x - c|, "
+                              "256x256 slice z = 0 masked inside, 64 walks/point, online training after every batch, "
+                              "16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 MLP, K = 8",
+                     grid=256, spp=64, eps=1e-3, maxsteps=128, l2="flushed (512 MiB write) before each step"),
+    "batch64": dict(workload="64 independent 2D star scenes (256-16384 segments log-uniform, Neumann fraction "
+                             "U(0.2, 0.5), 1k-256k points and 8-128 walks per point log-uniform), one persistent "
+                             "launch per training round under a CUDA graph, guided with online training per scene "
+                             "(and the plain batch for comparison)",
+                    scenes=64, eps=1e-3, maxsteps=128, l2="flushed (512 MiB write) before each step"),
+}
+
+
+def run_workload(args):
+    """Other workloads of the method (same metric and timing rules), for the
+    design notes: --workload sphere3d | batch64 on one GPU."""
+    import torch
+    import wost_inputs as wi
+    from paper_2410_18944_gb300 import api, build
+    build.build()
+    W = WORKLOADS[args.workload]
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    extra = {}
+    if args.workload == "sphere3d":
+        sc, pts_np = wi.config_3d_guided(res=W["grid"])
+        S = api.Scene(sc)
+        lo, hi = S.bbox()
+        F = api.Field(3, lo, hi, seed=1)
+        init = F.get_params()
+        pts = torch.tensor(pts_np, dtype=torch.float64, device=dev)
+
+        def solve(i, guided=True):
+            if guided:
+                F.set_params(init["grid"], init["W1"], init["W2"], init["W3"], init["b3"])
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[0].record(stream)
+            kw = dict(guided=True, field=F, train=1, train_until_wpp=256) if guided else {}
+            m, v, st = api.solve(S, pts, W["spp"], eps=W["eps"], maxsteps=W["maxsteps"], seed=i, stream=stream, **kw)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]), st["walk_steps"]
+        extra["points"] = len(pts_np)
+    else:
+        jobs = wi.config_batch()
+        scenes = [api.Scene(j.scene) for j in jobs]
+        pts = [torch.tensor(j.points, dtype=torch.float64, device=dev) for j in jobs]
+        plans = {}
+        for guided in (True, False):
+            specs = []
+            for i, j in enumerate(jobs):
+                d = dict(scene=scenes[i], points=pts[i], nwalks=j.nwalks, seed=j.seed, eps=W["eps"],
+                         maxsteps=W["maxsteps"])
+                if guided:
+                    lo, hi = scenes[i].bbox()
+                    d["field"] = api.Field(2, lo, hi, seed=1 + i)
+                specs.append(d)
+            plans[guided] = api.Batch(specs, guided=guided, train=1 if guided else 0)
+        extra["plan"] = {("guided" if g else "plain"): p.info() for g, p in plans.items()}
+        extra["points"] = sum(len(j.points) for j in jobs)
+        extra["walks"] = sum(len(j.points) * j.nwalks for j in jobs)
+
+        def solve(i, guided=True):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[0].record(stream)
+            st = plans[guided].run(stream.cuda_stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]), st["walk_steps"]
+    for i in range(args.warmup):
+        solve(i)
+    ms, steps = 0.0, 0
+    for i in range(args.steps):
+        t, n = solve(100 + i)
+        ms += t
+        steps += n
+    pms, psteps = solve(999, guided=False)
+    line = {"metric": METRIC, "value": steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 geometry, bf16 MLP, f64 accumulators", "data": "synthetic",
+            "config": dict(W, **extra), "plain_walk_steps_per_s": psteps / (pms / 1000.0)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_once(args):
     """One solve of (a seeded subset of) the workload, for profilers: no
     timing loop, no oracle.  --once plain|guided, --points N, --spp S."""
@@ -391,6 +482,8 @@ def run_once(args):
 
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", choices=["star2d", *WORKLOADS], default="star2d",
+                    help="star2d (the benchmark line) or another workload of the method")
     ap.add_argument("--once", choices=["plain", "guided"], default=None,
                     help="run one solve of the workload (profiling), no timing")
     ap.add_argument("--points", type=int, default=0, help="with --once: seeded subset of the query points")
@@ -412,6 +505,8 @@ def main():
         return run_once(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "star2d":
+        return run_workload(args)
     return run_ours(args)
 
 

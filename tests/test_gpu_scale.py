@@ -1,0 +1,102 @@
+"""Full-size GPU checks in the launch configuration the benchmark uses:
+
+* the 81,920-triangle displaced icosphere with all-Dirichlet data
+  g = 1/|x - c| (c outside, so u = g exactly): plain and guided walks against
+  the closed form on slice points;
+* the mixed Dirichlet / Neumann icosphere with Gaussian sources (no closed
+  form): guided walks with a frozen 3D field against the FP64 oracle at
+  sampled slice points, both sides drawing the same Philox streams;
+* the 4096-segment star with the benchmark's guided solve (online training
+  after every batch of one walk per point, 32 walks per point) against a
+  high-sample plain reference at every one of its 174,115 points: online
+  training changes the sampler, never the expectation."""
+import numpy as np
+import pytest
+
+import oracle
+import wost_inputs as wi
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2410_18944_gb300 import api as a, build
+    build.build()
+    return a
+
+
+def _random_field(api, dim, seed, sc, w_scale=1.0):
+    lo, hi = sc.padded_bbox()
+    F = api.Field(dim, lo, hi)
+    fp = wi.random_field_params(dim, seed, lo, hi, log2T=F.desc.log2_table, w_scale=w_scale)
+    fp["grid"] = wi.round_to_fp16(fp["grid"])
+    for k in ("W1", "W2", "W3"):
+        fp[k] = wi.round_to_bf16(fp[k])
+    fp["b3"] = fp["b3"].astype(np.float32).astype(np.float64)
+    F.set_params(fp["grid"], fp["W1"], fp["W2"], fp["W3"], fp["b3"])
+    return F, fp
+
+
+def test_icosphere_all_dirichlet_closed_form(api):
+    sc, pts = wi.config_3d_guided(neumann_frac=0.0, with_source=False)
+    assert len(sc.prims) == 81920 and (sc.bc == 0).all()
+    pts = wi.subsample(pts, 3000, seed=1)
+    S = api.Scene(sc)
+    pd = torch.tensor(pts, dtype=torch.float64, device="cuda")
+    ex = wi.eval_fn(sc.g, pts)
+    # near the boundary the walk values are heavy-tailed (most walks stop at
+    # once, a few travel far), so the sample variance of a finite number of
+    # walks runs small now and then: a few tenths of a percent of points
+    # may pass 4.5 estimated standard errors (checked with 20,000 walks and
+    # the FP64 oracle on the same random numbers)
+    m, v, st = api.solve(S, pd, 2048, eps=1e-3, maxsteps=512, seed=3)
+    z = (m.cpu().numpy() - ex) / np.sqrt(v.cpu().numpy())
+    assert st["truncated"] == 0
+    assert np.mean(np.abs(z) < 4.5) > 0.997 and abs(np.mean(z)) < 0.1, np.sort(np.abs(z))[-5:]
+    F, _ = _random_field(api, 3, 5, sc, w_scale=1.0)
+    m, v, st = api.solve(S, pd, 2048, eps=1e-3, maxsteps=512, seed=4, guided=True, field=F)
+    z = (m.cpu().numpy() - ex) / np.sqrt(v.cpu().numpy())
+    assert np.mean(np.abs(z) < 4.5) > 0.997 and abs(np.mean(z)) < 0.1, np.sort(np.abs(z))[-5:]
+
+
+def test_icosphere_mixed_guided_frozen_vs_oracle(api):
+    sc, pts = wi.config_3d_guided()
+    assert len(sc.prims) == 81920 and abs((sc.bc == 1).mean() - 0.3) < 0.01
+    pts = wi.subsample(pts, 16, seed=2)
+    S = api.Scene(sc)
+    F, fp = _random_field(api, 3, 6, sc, w_scale=1.0)
+    pd = torch.tensor(pts, dtype=torch.float64, device="cuda")
+    m, v, st = api.solve(S, pd, 4096, eps=1e-3, maxsteps=256, seed=8, guided=True, field=F)
+    m, v = m.cpu().numpy(), v.cpu().numpy()
+    OF = oracle.Field(oracle.FieldParams(**fp))
+    O = oracle.Scene(sc)
+    no = 96
+    r = oracle.solve(O, oracle.make_params(eps=1e-3, maxsteps=256, seed=8, guided=1), pts, 0, no, field=OF)
+    om, ov = oracle.mean_var(r["sum"], r["sum2"], no)
+    z = (m - om) / np.sqrt(v + ov)
+    assert np.all(np.isfinite(m)) and np.all(np.abs(z) < 4.5), z
+
+
+def test_star_benchmark_solve_is_unbiased_everywhere(api):
+    sc, pts = wi.config_star_guided(res=512)
+    assert len(pts) == 174115
+    S = api.Scene(sc)
+    lo, hi = S.bbox()
+    F = api.Field(2, lo, hi, seed=1)
+    pd = torch.tensor(pts, dtype=torch.float64, device="cuda")
+    m, v, st = api.solve(S, pd, 32, eps=1e-3, maxsteps=128, seed=11, guided=True, field=F, train=1,
+                         train_until_wpp=256)
+    assert st["train_steps"] == 32 and st["records_dropped"] == 0
+    mr, vr, _ = api.solve(S, pd, 1024, eps=1e-3, maxsteps=128, seed=12)
+    m, v, mr, vr = (t.cpu().numpy() for t in (m, v, mr, vr))
+    assert np.all(np.isfinite(m))
+    shell = (v == 0) & (vr == 0)          # eps-shell points: g at the closest point, both sides
+    assert shell.mean() < 0.01 and np.array_equal(m[shell], mr[shell])
+    z = (m - mr)[~shell] / np.sqrt(v + vr)[~shell]
+    assert np.mean(np.abs(z) < 4.5) > 0.9995, np.sort(np.abs(z))[-10:]
+    assert abs(np.mean(z)) < 0.02 and 0.9 < np.std(z) < 1.1, (np.mean(z), np.std(z))

@@ -452,6 +452,23 @@ def config_batch(njobs: int = 64, seed: int = 4, seg_range=(256, 16384), neumann
     return jobs
 
 
+def config_3d_guided(res: int = 256, subdiv: int = 6, seed: int = 3, neumann_frac: float = 0.3,
+                     with_source: bool = True, margin: float = 0.01):
+    """The displaced icosphere (81,920 triangles at subdiv 6) with its Neumann
+    cap, Gaussian sources and g = 1/|x - c|; query points are the res x res
+    cell centres of the slice z = 0 over the bounding box, kept where |p| is
+    below (1 - margin) of the displaced radius in p's direction (the surface
+    is star-shaped about the origin)."""
+    sc = displaced_icosphere(subdiv, seed, neumann_frac=neumann_frac, with_source=with_source)
+    lo, hi = sc.bbox
+    pts = slice_points_3d(res, lo, hi, 0.0)
+    noise = Perlin3(seed)
+    rad = np.linalg.norm(pts, axis=1)
+    d = pts / np.maximum(rad, 1e-12)[:, None]
+    r_surf = 1 + 0.15 * noise(d * 2.0 + 17.0)
+    return sc, pts[rad < (1 - margin) * r_surf]
+
+
 def subsample(pts: np.ndarray, n: int, seed: int = 0) -> np.ndarray:
     if n >= len(pts):
         return pts
