@@ -20,11 +20,16 @@
 //              its geometry, claims a 32-row quarter of a decode tile, writes
 //              its features, and waits only for that tile.
 // Tiles are formed from whichever walker warps are ready (quarters are claimed
-// in order from a shared counter), through rings of mbarriers over kNT tile
-// buffers: full (4 quarter arrivals), done (one per quarter), empty (4
-// consumer arrivals).  When a tile stays partly claimed the server closes it
-// (compare-and-swap on the claim counter) and zero-pads the missing quarters,
-// so a few remaining walkers never wait for partners that will not come.
+// in order from a shared counter) over kNT tile buffers: mbarriers `full`
+// (4 quarter arrivals) and `done` (one per quarter), and per buffer a count
+// of consumed quarters.  A claimant of tile T reuses buffer T % kNT only once
+// all 4 (T / kNT) quarters of its earlier tiles are consumed: tiles can be
+// consumed out of order (a walker holds its row while its geometry runs), so
+// a parity wait on a barrier could mistake an old phase for the one it
+// needs; the monotonic count cannot.  When a tile stays partly claimed the
+// server closes it (compare-and-swap on the claim counter) and zero-pads the
+// missing quarters, so a few remaining walkers never wait for partners that
+// will not come.
 // Every wait is bounded; a give-up sets the error word and ends the loops.
 //
 // Multi-scene tiles: each row records the job of its walk.  The server runs
@@ -55,12 +60,9 @@ constexpr int kWsThreads = 32 * (kWsServerWarps + kWsWalkerWarps);
 constexpr int kNT = WOST_WS_TILES;           // decode tile buffers (few: leaves L1 for the BVH)
 constexpr uint32_t kWsTmemCols = tmem_cols(kNT * 64);   // allocation rounded up to a power of two
 static_assert(kNT >= 1 && kNT * 64 <= 512, "decode tile buffers must fit in the 512 TMEM columns");
-// mbarrier parity waits only tell phase k from k+1: the tiles a buffer can
-// be asked for must never run two generations ahead of its consumption.  The
-// outstanding claims (one per walker warp) span at most floor((W + 2) / 4)
-// tiles beyond the oldest one, and a claim in tile T waits for tile T - kNT.
-static_assert((kWsWalkerWarps + 2) / 4 <= 2 * kNT - 1,
-              "too many walker warps for the decode tile ring (parity waits would alias)");
+// The `full` and `done` barriers of a buffer can never run two phases ahead
+// of their waiters: a tile's quarters arrive only after the tile kNT earlier
+// is consumed, which follows its `done`, which follows its `full`.
 constexpr int kXTileBytes = 128 * kFeat * 2;
 constexpr int kHTileBytes = 128 * kHid * 2;
 constexpr int kYStride = 50;                 // FP16 output row stride (25 words: conflict-free)
@@ -78,10 +80,17 @@ constexpr int ws_smem_bytes(bool multi) {
            (multi ? kNT * (128 * 4 + kYBytes) : 0);
 }
 constexpr uint32_t kFlushPolls = 256;        // server polls before closing a partial tile
-constexpr uint32_t kWaitLimit = 1u << 22;    // bound of every wait loop
+// Decode in flight during the step's geometry.  Measured on the 2D star
+// workload it is slower (the terminal steps' decodes are wasted and tile
+// buffers stay held through the geometry), so it is off by default.
+#ifndef WOST_WS_OVERLAP
+#define WOST_WS_OVERLAP 0
+#endif
+constexpr bool kOverlap = WOST_WS_OVERLAP != 0;
 
 struct WsCtrl {
-    uint64_t full[kNT], done[kNT][4], empty[kNT], mma;
+    uint64_t full[kNT], done[kNT][4], mma;
+    unsigned consumed[kNT];   // quarters of the buffer's tiles consumed so far
     int qclaim, alive, go, padmask;
     uint32_t tmem;
     int pick, wnext;
@@ -106,11 +115,24 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" : : "r"(smem_u32(bar)) : "memory");
 }
 
-// all lanes of the calling warp poll; returns false on give-up
+// all lanes of the calling warp poll (converged); returns false on give-up
 __device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    return mbar_wait_bounded(bar, parity);
+}
+
+// until *count reaches target (monotonic); false on give-up
+__device__ __forceinline__ bool wait_consumed(const unsigned *count, unsigned target) {
+    if (*(volatile const unsigned *)count >= target) {
+        __threadfence_block();
+        return true;
+    }
+    const unsigned long long t0 = globaltimer_ns();
+    while (*(volatile const unsigned *)count < target) {
+        if (globaltimer_ns() - t0 > kWaitNs) return false;
+        __nanosleep(64);
+    }
+    __threadfence_block();
+    return true;
 }
 
 __device__ __forceinline__ void zero_row(uint8_t *tile, int row, int C) {
@@ -163,7 +185,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
     if (tid == 0) {
         for (int b = 0; b < kNT; ++b) {
             mbar_init(&ctl->full[b], 4);
-            mbar_init(&ctl->empty[b], 4);
+            ctl->consumed[b] = 0;
             for (int q = 0; q < 4; ++q) mbar_init(&ctl->done[b][q], 1);
         }
         mbar_init(&ctl->mma, 1);
@@ -193,8 +215,10 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
             if (tid == 0) {
                 int go = -1, pad = 0;
                 uint32_t polls = 0;
-                for (uint32_t it = 0; it < kWaitLimit; ++it) {
+                const unsigned long long t0 = globaltimer_ns();
+                for (;;) {
                     if (mbar_try_wait(&ctl->full[b], k & 1u)) { go = 1; break; }
+                    if (globaltimer_ns() - t0 > kWaitNs) break;
                     if (++polls < o.flush_polls) continue;
                     polls = 0;
                     int q = *(volatile int *)&ctl->qclaim;
@@ -270,7 +294,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
                         else umma_gemm(tm, Hb(b), 0, kHid, wimg + kW1Bytes + kW2Bytes, 0, kHid, kOutPad, kHid, false);
                         umma_commit(&ctl->mma);
                     }
-                    ok = mbar_wait_bounded(&ctl->mma, mma_phase, kWaitLimit);
+                    ok = mbar_wait_bounded(&ctl->mma, mma_phase);
                     mma_phase ^= 1u;
                     tc_fence_after();
                     ok = !named_or(1, 128, !ok);
@@ -325,7 +349,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&ctl->done[b][warp]);
-                if (pad & (1 << warp)) mbar_arrive(&ctl->empty[b]);   // no consumer for a padded quarter
+                if (pad & (1 << warp)) atomicAdd(&ctl->consumed[b], 1u);   // no consumer for a padded quarter
             }
         }
     } else {
@@ -344,33 +368,46 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
             if (!__any_sync(0xffffffffu, active || !exhausted)) break;
             __syncwarp();
             float r = 0.f, S = 0.f;
-            if (active) {
-                nsteps++;
-                float gv;
-                bool trunc = false;
-                if (step_geometry<D>(w, src.env(w), r, S, gv, trunc, &vis)) {
-                    src.finish(w);
-                    if (o.record) end_recorded_walk(src.rec(w), scratch_row, w.k, gv);
-                    ntrunc += trunc;
-                    active = false;
+            // The decode needs only the walk's position: with kOverlap the
+            // row is submitted first and the step's geometry runs while the
+            // tile fills and decodes (a walk that then ends leaves its row
+            // unused).  Otherwise the geometry runs first and only walks that
+            // go on are decoded.
+            auto geometry = [&]() {
+                if (active) {
+                    nsteps++;
+                    float gv;
+                    bool trunc = false;
+                    if (step_geometry<D>(w, src.env(w), r, S, gv, trunc, &vis)) {
+                        src.finish(w);
+                        if (o.record) end_recorded_walk(src.rec(w), scratch_row, w.k, gv);
+                        ntrunc += trunc;
+                        active = false;
+                    }
                 }
-            }
-            const bool live = active;
-            if (!__any_sync(0xffffffffu, live)) continue;
+            };
+            if (!kOverlap) geometry();
+            const bool enc = active;
+            if (!__any_sync(0xffffffffu, enc)) continue;
             // claim a quarter of a decode tile
             int qi = 0;
             if (lane == 0) qi = atomicAdd(&ctl->qclaim, 1);
             qi = __shfl_sync(0xffffffffu, qi, 0);
             const int T = qi >> 2, quarter = qi & 3, b = T % kNT;
             const uint32_t k = (uint32_t)(T / kNT);
-            if (T >= kNT && !ws_wait(&ctl->empty[b], (k - 1u) & 1u)) { failed = true; break; }
+            if (T >= kNT && !wait_consumed(&ctl->consumed[b], 4u * k)) { failed = true; break; }
             const int row = 32 * quarter + lane;
-            if (live) encode_row<D>(src.field(w), w.x, Xb(b), row);
+            if (enc) encode_row<D>(src.field(w), w.x, Xb(b), row);
             else zero_row(Xb(b), row, kFeat);
-            if (kMulti) rowjob[b * 128 + row] = live ? src.job(w) : -1;
+            if (kMulti) rowjob[b * 128 + row] = enc ? src.job(w) : -1;
             fence_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->full[b]);
+            if (kOverlap) geometry();
+            // reconverge before polling: lanes without a step must not spin
+            // on the barrier while the others' geometry runs
+            __syncwarp();
+            const bool live = active;
             if (!ws_wait(&ctl->done[b][quarter], k & 1u)) { failed = true; break; }
             float nu[D];
             bool zero_density = false;
@@ -404,7 +441,10 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
                 }
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&ctl->empty[b]);   // tile rows consumed
+            if (lane == 0) {   // tile rows consumed
+                __threadfence_block();
+                atomicAdd(&ctl->consumed[b], 1u);
+            }
             if (live) {
                 if (zero_density) {
                     src.finish(w);

@@ -125,11 +125,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait: false after `limit` polls (the caller reports a timeout)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit = 1u << 20) {
-    for (uint32_t i = 0; i < limit; ++i)
+// Waits are bounded by time, not by poll count: a failing try_wait may
+// suspend the warp for a hardware-chosen while, so a poll count says little
+// about how long a wait lasts.
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait: false once kWaitNs have passed (the caller reports a timeout)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-    return false;
+        if (globaltimer_ns() - t0 > kWaitNs) return false;
+    }
 }
 
 // named barrier over `count` threads and an OR-reduction over it
