@@ -302,6 +302,36 @@ def run_ours(args):
     torch.cuda.synchronize()
     plain_rate = stp["walk_steps"] / (ev[0].elapsed_time(ev[1]) / 1000.0)
 
+    # the tensor-core decode on its own: 4 Mi positions through
+    # wost_field_decode (hash-grid encode + three tcgen05 BF16 MMAs per
+    # 128-row tile), device buffers, CUDA events on the stream
+    ndec = 1 << 22
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    lo_t = torch.tensor(lo, dtype=torch.float64, device=dev)
+    hi_t = torch.tensor(hi, dtype=torch.float64, device=dev)
+    dec_pts = lo_t + (hi_t - lo_t) * torch.rand((ndec, 2), dtype=torch.float64, device=dev, generator=g)
+    dec_out = torch.empty((ndec, F.nout), dtype=torch.float32, device=dev)
+    for _ in range(2):
+        F.decode(dec_pts, out=dec_out, exec_=api.exec_defaults(stream=stream))
+    flush.zero_()
+    torch.cuda.synchronize()
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev[0].record(stream)
+    F.decode(dec_pts, out=dec_out, exec_=api.exec_defaults(stream=stream))
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    dec_s = ev[0].elapsed_time(ev[1]) / 1000.0
+    flop_per = 2.0 * (32 * 64 + 64 * 64 + 64 * 48)       # padded output width 48
+    bf16_peak = measured_peaks().get("bf16_tflops")
+    dec_tflops = ndec * flop_per / dec_s / 1e12
+    decode = {"points": ndec, "ms": dec_s * 1e3, "decodes_per_s": ndec / dec_s, "bound": "tensor",
+              "achieved_tflops": dec_tflops, "peak_tflops": bf16_peak or 1900.0,
+              "frac": dec_tflops / (bf16_peak or 1900.0),
+              "peak_source": "measured" if bf16_peak else "fallback",
+              "note": "per point 18.4 kFLOP of BF16 MMA against 64 hash-grid corner gathers (L2): "
+                      "the encode gathers, not the tensor pipe, set the decode time"}
+
     # equal-time relMSE (guided with training vs plain), against a plain
     # reference at 16x the walks per point; relMSE = mean (u^ - u)^2 / (u^2 + 1e-2)
     relmse = None
@@ -336,8 +366,17 @@ def run_ours(args):
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
     achieved = (alg / walk_launches) / ((walk_ms / walk_launches) / 1000.0) / 1e9
+    traffic = args.traffic
+    if traffic is None:
+        # DRAM bytes per walk-step of the walk kernel from its ncu capture,
+        # scaled to this run's walk-steps per launch
+        try:
+            tr = json.load(open(os.path.join(ROOT, "profiles", "guided_walk_traffic.json")))
+            traffic = tr["dram_bytes_per_walk_step"] * sum(s["walk_steps"] for s in stats) / walk_launches
+        except (OSError, ValueError, KeyError):
+            traffic = None
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": args.traffic, "kernel": "guided_walk_kernel<2>", "peak_source": peak_src,
+            "traffic": traffic, "kernel": "guided_walk_kernel<2>", "peak_source": peak_src,
             "alg_bytes_per_walk_step": alg / sum(s["walk_steps"] for s in stats)}
 
     cpu_rate, cpu_info = (None, {})
@@ -360,6 +399,7 @@ def run_ours(args):
                           "walk_steps_per_step": steps_local / len(stats),
                           "records_per_step": sum(s["records"] for s in stats) / len(stats)},
             "plain_walk_steps_per_s": plain_rate,
+            "decode": decode,
             "relmse": relmse}
     print(json.dumps(line), flush=True)
     return 0

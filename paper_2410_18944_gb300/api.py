@@ -165,10 +165,22 @@ class Field:
                                                         ("grid", "W1", "W2", "W3", "b3")]))
         return out
 
-    def decode(self, pts, exec_=None):
+    def decode(self, pts, exec_=None, out=None):
+        """wost_field_decode: raw outputs (n, nout).  ``pts`` is a numpy array
+        (host) or a CUDA float64 tensor (device; then the result is a CUDA
+        float32 tensor, ``out`` optional)."""
+        e = exec_ or exec_defaults()
+        if _is_cuda_tensor(pts):
+            import torch
+            if out is None:
+                out = torch.empty((pts.shape[0], self.nout), dtype=torch.float32, device=pts.device)
+            e.points_on_device = 1
+            e.out_on_device = 1
+            check(L.load().wost_field_decode(self._h, C.c_void_p(pts.data_ptr()), pts.shape[0],
+                                             C.c_void_p(out.data_ptr()), C.byref(e)))
+            return out
         p = np.ascontiguousarray(pts, np.float64)
         out = np.zeros((len(p), self.nout), np.float32)
-        e = exec_ or exec_defaults()
         check(L.load().wost_field_decode(self._h, p.ctypes.data_as(C.c_void_p), len(p),
                                          out.ctypes.data_as(C.c_void_p), C.byref(e)))
         return out
