@@ -6,6 +6,9 @@
 * the mixed Dirichlet / Neumann icosphere with Gaussian sources (no closed
   form): guided walks with a frozen 3D field against the FP64 oracle at
   sampled slice points, both sides drawing the same Philox streams;
+* the 1 M-triangle genus-3 mesh: all-Dirichlet closed form, and plain walks
+  against the brute-force FP64 oracle on the same Philox streams, guided
+  against plain;
 * the 4096-segment star with the benchmark's guided solve (online training
   after every batch of one walk per point, 32 walks per point) against a
   high-sample plain reference at every one of its 174,115 points: online
@@ -100,3 +103,62 @@ def test_star_benchmark_solve_is_unbiased_everywhere(api):
     z = (m - mr)[~shell] / np.sqrt(v + vr)[~shell]
     assert np.mean(np.abs(z) < 4.5) > 0.9995, np.sort(np.abs(z))[-10:]
     assert abs(np.mean(z)) < 0.02 and 0.9 < np.std(z) < 1.1, (np.mean(z), np.std(z))
+
+
+@pytest.fixture(scope="module")
+def genus3():
+    return wi.config_genus3()
+
+
+def test_genus3_mesh_is_the_large_workload(genus3):
+    sc, pts = genus3
+    assert 0.95e6 < len(sc.prims) < 1.05e6 and abs((sc.bc == 1).mean() - 0.3) < 0.001
+    assert len(pts) > 400000
+    # closed, consistently outward-wound, genus 3 (Euler characteristic -4)
+    V, P = sc.verts, sc.prims
+    a, b, c = V[P[:, 0]], V[P[:, 1]], V[P[:, 2]]
+    assert np.einsum("ij,ij->i", a, np.cross(b, c)).sum() / 6 > 3.0
+    e = np.concatenate([P[:, [0, 1]], P[:, [1, 2]], P[:, [2, 0]]], 0).astype(np.int64)
+    key, rev = e[:, 0] * len(V) + e[:, 1], e[:, 1] * len(V) + e[:, 0]
+    assert len(np.unique(key)) == len(key) and np.array_equal(np.sort(key), np.sort(rev))
+    assert len(V) - len(e) // 2 + len(P) == -4
+
+
+def test_genus3_all_dirichlet_closed_form(api, genus3):
+    sc, pts = genus3
+    scd = wi.Scene("genus3_dirichlet", 3, sc.verts, sc.prims, np.zeros_like(sc.bc), sc.g)
+    S = api.Scene(scd)
+    p = wi.subsample(pts, 2000, seed=3)
+    pd = torch.tensor(p, dtype=torch.float64, device="cuda")
+    ex = wi.eval_fn(scd.g, p)
+    m, v, st = api.solve(S, pd, 2048, eps=1e-3, maxsteps=512, seed=5)
+    z = (m.cpu().numpy() - ex) / np.sqrt(v.cpu().numpy())
+    assert np.mean(np.abs(z) < 4.5) > 0.997 and abs(np.mean(z)) < 0.1, np.sort(np.abs(z))[-5:]
+
+
+def test_genus3_mixed_vs_oracle_same_streams(api, genus3):
+    sc, pts = genus3
+    p = wi.subsample(pts, 16, seed=4)
+    S = api.Scene(sc)
+    pd = torch.tensor(p, dtype=torch.float64, device="cuda")
+    # the oracle's queries are brute force over all 1 M triangles (seconds
+    # per walk), so it runs 8 walks per point; the device solve takes the
+    # same 8 Philox streams, and the two walks coincide step for step until
+    # an FP32 decision differs, so most points agree to rounding
+    no = 8
+    m8, _, _ = api.solve(S, pd, no, eps=1e-3, maxsteps=256, seed=10)
+    O = oracle.Scene(sc)
+    r = oracle.solve(O, oracle.make_params(eps=1e-3, maxsteps=256, seed=10), p, 0, no)
+    om, ov = oracle.mean_var(r["sum"], r["sum2"], no)
+    m8 = m8.cpu().numpy()
+    close = np.abs(m8 - om) <= 1e-4 * np.abs(om) + 1e-6
+    assert close.mean() >= 0.5, np.abs(m8 - om) / np.abs(om)
+    # plain and guided (frozen random field) solves with many walks agree
+    # with each other and, loosely, with the oracle's few walks
+    mp, vp, _ = api.solve(S, pd, 4096, eps=1e-3, maxsteps=256, seed=11)
+    F, _ = _random_field(api, 3, 9, sc, w_scale=1.0)
+    mg, vg, _ = api.solve(S, pd, 4096, eps=1e-3, maxsteps=256, seed=12, guided=True, field=F)
+    mp, vp, mg, vg = (t.cpu().numpy() for t in (mp, vp, mg, vg))
+    assert np.all(np.isfinite(mg)) and np.all(np.abs((mg - mp) / np.sqrt(vg + vp)) < 4.5)
+    zo = (mp - om) / np.sqrt(vp + ov + 1e-30)
+    assert np.sum(zo[ov > 0] ** 2) < 3 * max(1, (ov > 0).sum()), zo

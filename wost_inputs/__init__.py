@@ -288,6 +288,140 @@ def displaced_icosphere(subdiv: int = 6, seed: int = 3, amp: float = 0.15, freq:
     return Scene(f"icosphere{subdiv}_s{seed}", 3, v, f, bc, Fn(FN_INV_DIST, [2.5, 0.0, 0.0]), f=src)
 
 
+def _tunnel_lines(rng, count=3, radius=0.2, reach=0.45, min_gap=0.5):
+    """Seeded lines (point, unit direction) crossing the unit ball, pairwise
+    at least min_gap apart, so the tunnels around them are disjoint."""
+    lines = []
+    while len(lines) < count:
+        a = rng.normal(size=3)
+        a /= np.linalg.norm(a)
+        p = rng.normal(size=3)
+        p -= (p @ a) * a
+        p *= rng.uniform(0.0, reach) / max(np.linalg.norm(p), 1e-12)
+        ok = True
+        for q, b in lines:
+            n = np.cross(a, b)
+            dist = abs((p - q) @ n) / np.linalg.norm(n) if np.linalg.norm(n) > 1e-9 else \
+                np.linalg.norm(np.cross(p - q, a))
+            ok &= dist > min_gap
+        if ok:
+            lines.append((p, a))
+    return lines
+
+
+def genus3_sdf(pts: np.ndarray, seed: int = 5, amp: float = 0.15, freq: float = 2.0, radius: float = 0.2,
+               blend: float = 0.04):
+    """Signed distance-like function (negative inside) of the displaced unit
+    sphere minus three disjoint cylinders of the given radius along seeded
+    lines: smax(|p| - R(p/|p|), -(dist_i - radius)), where smax is the
+    polynomial smooth maximum max(a, b) + k h^2 / 4, h = max(k - |a - b|, 0) / k
+    with k = blend, which rounds the tunnel rims so that no crease is sharper
+    than the meshing grid.  R is evaluated only in the radial band where the
+    displaced surface can lie."""
+    rng = np.random.default_rng(seed)
+    noise = Perlin3(seed)
+    lines = _tunnel_lines(rng, radius=radius)
+    pts = np.asarray(pts, np.float64)
+    r = np.linalg.norm(pts, axis=1)
+    d = r - 1.0
+    band = (r > 1 - 1.2 * amp) & (r < 1 + 1.2 * amp)
+    if band.any():
+        dirs = pts[band] / r[band][:, None]
+        d[band] = r[band] - (1 + amp * noise(dirs * freq + 17.0))
+    for p0, a in lines:
+        q = pts - p0
+        q -= (q @ a)[:, None] * a
+        e = radius - np.linalg.norm(q, axis=1)
+        h = np.maximum(blend - np.abs(d - e), 0.0) / blend
+        d = np.maximum(d, e) + 0.25 * blend * h * h
+    return d
+
+
+def surface_nets(sdf, n: int, lo: float, hi: float, chunk: int = 1 << 22):
+    """Naive surface nets of the zero level set of sdf (negative inside) on an
+    n^3-cell grid over [lo, hi]^3: one vertex per cell with a sign change (the
+    mean of its edges' linear crossings), one quad per crossing grid edge over
+    the four cells sharing it, wound counter-clockwise seen from outside, split
+    into two triangles.  Returns (verts, tris)."""
+    h = (hi - lo) / n
+    axis = lo + h * np.arange(n + 1)
+    X, Y, Z = np.meshgrid(axis, axis, axis, indexing="ij")
+    P = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    del X, Y, Z
+    s = np.empty(len(P))
+    for b in range(0, len(P), chunk):
+        s[b:b + chunk] = sdf(P[b:b + chunk])
+    del P
+    s = s.reshape(n + 1, n + 1, n + 1)
+    inside = s < 0
+    assert not inside[[0, -1]].any() and not inside[:, [0, -1]].any() and not inside[:, :, [0, -1]].any()
+    cell_ids, cross_pts, quads, flips = [], [], [], []
+
+    def cid(i, j, k):
+        return (i * n + j) * n + k
+
+    for ax in range(3):
+        sl0 = [slice(None)] * 3
+        sl1 = [slice(None)] * 3
+        sl0[ax] = slice(0, n)
+        sl1[ax] = slice(1, n + 1)
+        ch = inside[tuple(sl0)] != inside[tuple(sl1)]
+        idx = np.argwhere(ch)                      # lower endpoint (i, j, k)
+        s0 = s[tuple(sl0)][ch]
+        s1 = s[tuple(sl1)][ch]
+        t = s0 / (s0 - s1)
+        p = lo + h * idx.astype(np.float64)
+        p[:, ax] += h * t
+        i, j, k = idx[:, 0], idx[:, 1], idx[:, 2]
+        # the four cells around the edge, counter-clockwise about +axis
+        if ax == 0:
+            cs = [cid(i, j - 1, k - 1), cid(i, j, k - 1), cid(i, j, k), cid(i, j - 1, k)]
+        elif ax == 1:
+            cs = [cid(i - 1, j, k - 1), cid(i - 1, j, k), cid(i, j, k), cid(i, j, k - 1)]
+        else:
+            cs = [cid(i - 1, j - 1, k), cid(i, j - 1, k), cid(i, j, k), cid(i - 1, j, k)]
+        cs = np.stack(cs, 1)
+        for c in range(4):
+            cell_ids.append(cs[:, c])
+            cross_pts.append(p)
+        quads.append(cs)
+        flips.append(s0 >= 0)                       # outside (not s < 0) at the lower end: outward is -axis
+    ids = np.concatenate(cell_ids)
+    pts = np.concatenate(cross_pts, 0)
+    uniq, inv = np.unique(ids, return_inverse=True)
+    cnt = np.bincount(inv, minlength=len(uniq))
+    verts = np.stack([np.bincount(inv, weights=pts[:, d], minlength=len(uniq)) / cnt for d in range(3)], 1)
+    q = np.searchsorted(uniq, np.concatenate(quads, 0))
+    flip = np.concatenate(flips)
+    q[flip] = q[flip][:, ::-1]
+    tris = np.concatenate([q[:, [0, 1, 2]], q[:, [0, 2, 3]]], 0).astype(np.int32)
+    return verts, tris
+
+
+def genus3_mesh(n: int = 330, seed: int = 5, neumann_frac: float = 0.3) -> Scene:
+    """The genus-3 solid (displaced sphere minus three disjoint tunnels) as a
+    naive-surface-nets mesh on an n^3 grid over [-1.25, 1.25]^3 (about 1 M
+    triangles at n = 330); the Neumann set is the neumann_frac of faces whose
+    centroid direction best aligns with a seeded axis; Dirichlet g = 1/|x - c|,
+    c = (2.5, 0, 0); no source."""
+    verts, tris = surface_nets(lambda p: genus3_sdf(p, seed), n, -1.25, 1.25)
+    rng = np.random.default_rng(seed + 1000)
+    axis = rng.normal(size=3)
+    axis /= np.linalg.norm(axis)
+    bc = _cap_neumann(verts, tris, neumann_frac, axis)
+    return Scene(f"genus3_n{n}_s{seed}", 3, verts, tris, bc, Fn(FN_INV_DIST, [2.5, 0.0, 0.0]))
+
+
+def config_genus3(res: int = 1024, n: int = 330, seed: int = 5, margin: float = 0.02):
+    """The large 3D workload: the genus-3 mesh and the res x res cell centres
+    of the slice z = 0 over its bounding box, kept where the solid's signed
+    function is below -margin (inside, off the boundary)."""
+    sc = genus3_mesh(n, seed)
+    lo, hi = sc.bbox
+    pts = slice_points_3d(res, lo, hi, 0.0)
+    return sc, pts[genus3_sdf(pts, seed) < -margin]
+
+
 def slab_box(n: int = 4) -> Scene:
     """Box [-1,1]^2 x [0,1] triangulated with n x n quads per face; the
     faces z = 0 and z = 1 are zero-flux Neumann, the side faces Dirichlet with
