@@ -124,6 +124,12 @@ typedef struct {
                                   all draw the same random numbers */
     int32_t wavefront_slots;   /* walks in flight in a wavefront launch that trains nothing
                                   (0 = 2^20); a launch that trains holds one walk per point */
+    int64_t train_samples;     /* records per training step (Sec. 5.2, online training on
+                                  fixed-size batches): 0 = every record of the batch; otherwise,
+                                  with n records and n > train_samples, the step uses records
+                                  o, o + k, o + 2k, ... < n with k = ceil(n / train_samples) and
+                                  o = (t * 2654435761) mod k, t the field's Adam step count
+                                  before the step (so consecutive steps take different strata) */
 } wost_exec;
 
 typedef struct {

@@ -45,7 +45,8 @@ class Exec(C.Structure):
                 ("out_on_device", C.c_int32), ("c_mode", C.c_int32), ("c_fixed", C.c_float),
                 ("reflect", C.c_int32), ("train", C.c_int32), ("train_until_wpp", C.c_int32),
                 ("max_train_records", C.c_int64), ("walk_begin", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("guided_kernel", C.c_int32), ("wavefront_slots", C.c_int32)]
+                ("guided_kernel", C.c_int32), ("wavefront_slots", C.c_int32),
+                ("train_samples", C.c_int64)]
 
 
 class Stats(C.Structure):

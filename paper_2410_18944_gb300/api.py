@@ -198,10 +198,12 @@ class Field:
         check(L.load().wost_get_records(self._h, out.ctypes.data_as(L._fp), m, C.byref(n)))
         return out
 
-    def train_grad(self):
+    def train_grad(self, samples=0):
+        """wost_train_grad on the record buffer (all records, or the strided
+        subset of about ``samples`` records, exec train_samples)."""
         g = {k: np.zeros(s, np.float32) for k, s in self.shapes().items()}
         loss = C.c_float()
-        e = exec_defaults()
+        e = exec_defaults(train_samples=int(samples))
         check(L.load().wost_train_grad(self._h, C.byref(e), C.byref(loss),
                                        *[g[k].ctypes.data_as(L._fp) for k in ("grid", "W1", "W2", "W3", "b3")]))
         return loss.value, g

@@ -386,6 +386,7 @@ wost_status build_plan(wost_batch *p) {
             f->t_c_mode = ex.c_mode;
             f->t_c_fixed = ex.c_fixed;
             f->t_reflect = ex.reflect;
+            f->t_samples = ex.train_samples;
             p->hjobs[j].rd = RecDest{f->rec, f->rec_ctr, f->rec_cap};
         }
         if ((rc = upload(p->djobs, p->hjobs)) != WOST_OK) return rc;

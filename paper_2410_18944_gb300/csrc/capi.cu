@@ -182,7 +182,7 @@ extern "C" wost_status wost_create_field(const wost_field_desc *desc, wost_field
     if (rc == WOST_OK) rc = alloc((void **)&f->grid16, (ng / 2) * sizeof(__half2));
     if (rc == WOST_OK) rc = alloc((void **)&f->wimg, kWImgBytes);
     if (rc == WOST_OK) rc = alloc((void **)&f->b3pad, kOutPad * sizeof(float));
-    if (rc == WOST_OK) rc = alloc((void **)&f->loss_acc, 2 * sizeof(double));
+    if (rc == WOST_OK) rc = alloc((void **)&f->loss_acc, 3 * sizeof(double));
     if (rc != WOST_OK) { delete f; return rc; }
     std::vector<float> grid, mlp;
     init_params(d, f->nout, ng, grid, mlp);
@@ -193,7 +193,7 @@ extern "C" wost_status wost_create_field(const wost_field_desc *desc, wost_field
     if (e == cudaSuccess) e = cudaMemset(f->mlp_m, 0, nm * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(f->mlp_v, 0, nm * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(f->wimg, 0, kWImgBytes);
-    if (e == cudaSuccess) e = cudaMemset(f->loss_acc, 0, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(f->loss_acc, 0, 3 * sizeof(double));
     if (e != cudaSuccess) { delete f; return cuda_status(e, "wost_create_field"); }
     if ((rc = refresh_inference_copy(f, 0)) != WOST_OK) { delete f; return rc; }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) { delete f; return cuda_status(e, "wost_create_field"); }
@@ -255,6 +255,7 @@ extern "C" wost_status wost_train_records(wost_field *f, const float *records, i
     f->t_c_mode = ex.c_mode;
     f->t_c_fixed = ex.c_fixed;
     f->t_reflect = ex.reflect;
+    f->t_samples = ex.train_samples;
     return WOST_OK;
 }
 
@@ -273,13 +274,12 @@ extern "C" wost_status wost_get_records(const wost_field *f, float *records, int
 }
 
 static wost_status read_loss(wost_field *f, cudaStream_t st, float *out_loss) {
-    double l = 0;
-    unsigned long long c[2];
-    WOST_CUDA(cudaMemcpyAsync(&l, f->loss_acc, sizeof(double), cudaMemcpyDeviceToHost, st));
-    WOST_CUDA(cudaMemcpyAsync(c, f->rec_ctr, sizeof(c), cudaMemcpyDeviceToHost, st));
+    double acc[3] = {0, 0, 0};
+    WOST_CUDA(cudaMemcpyAsync(acc, f->loss_acc, sizeof(acc), cudaMemcpyDeviceToHost, st));
     WOST_CUDA(cudaStreamSynchronize(st));
-    int64_t n = (int64_t)std::min<unsigned long long>(c[0], (unsigned long long)f->rec_cap);
-    if (out_loss) *out_loss = n > 0 ? (float)(l / n) : 0.f;
+    unsigned long long n;
+    std::memcpy(&n, &acc[2], sizeof(n));
+    if (out_loss) *out_loss = n > 0 ? (float)(acc[0] / (double)n) : 0.f;
     return WOST_OK;
 }
 
@@ -288,6 +288,7 @@ extern "C" wost_status wost_train_step(wost_scene *s, wost_field *f, const wost_
     if (s && s->dim != f->desc.dim) { set_error("wost_train_step: dimension mismatch"); return WOST_ERR_INVALID_ARG; }
     if (!f->rec || !f->rec_ctr) { set_error("wost_train_step: no training records"); return WOST_ERR_INVALID_ARG; }
     cudaStream_t st = exec ? (cudaStream_t)exec->stream : 0;
+    if (exec) f->t_samples = exec->train_samples;
     wost_status rc = train_launch(f, f->desc.dim, st, true, nullptr);
     if (rc != WOST_OK) return rc;
     if ((rc = read_loss(f, st, out_loss)) != WOST_OK) return rc;
@@ -299,6 +300,7 @@ extern "C" wost_status wost_train_grad(wost_field *f, const wost_exec *exec, flo
     if (!f) { set_error("wost_train_grad: null field"); return WOST_ERR_INVALID_ARG; }
     if (!f->rec || !f->rec_ctr) { set_error("wost_train_grad: no training records"); return WOST_ERR_INVALID_ARG; }
     cudaStream_t st = exec ? (cudaStream_t)exec->stream : 0;
+    if (exec) f->t_samples = exec->train_samples;
     wost_status rc = train_launch(f, f->desc.dim, st, false, nullptr);
     if (rc != WOST_OK) return rc;
     if ((rc = read_loss(f, st, out_loss)) != WOST_OK) return rc;

@@ -259,12 +259,15 @@ struct wost_field {
     unsigned long long *rec_ctr = nullptr;   // [0] count, [1] dropped
     float *scratch = nullptr;
     size_t scratch_bytes = 0;
-    float *loss_acc = nullptr;               // [0] FP64 loss sum, [1] Adam step count (u64)
+    float *loss_acc = nullptr;               // [0] FP64 loss sum, [1] Adam step count (u64),
+                                             // [2] records the last step used (u64)
     // the Adam step count lives on the device so that a captured graph of
     // training steps advances it on every replay
     unsigned long long *adam_step() const { return reinterpret_cast<unsigned long long *>(loss_acc) + 1; }
+    unsigned long long *used_records() const { return reinterpret_cast<unsigned long long *>(loss_acc) + 2; }
     int t_c_mode = 0, t_reflect = 1;         // MIS options of the records in the buffer
     float t_c_fixed = 0.5f;
+    int64_t t_samples = 0;                   // records per training step (0 = all)
     int64_t n_mlp() const {
         int H = desc.hidden, nin = desc.levels * desc.features;
         return (int64_t)H * nin + (int64_t)H * H + (int64_t)nout * H + nout;

@@ -155,6 +155,7 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
     f->t_c_mode = ex.c_mode;
     f->t_c_fixed = ex.c_fixed;
     f->t_reflect = ex.reflect;
+    f->t_samples = ex.train_samples;
     // Launch selection.  A launch that records training data holds one walk
     // per point (the field trains after it), and its time is set by how fast
     // walkers finish a few walks each: the asynchronous warp-specialised

@@ -46,6 +46,9 @@ struct TrainArgs {
     float *g_grid;   // L x T x F
     float *g_W1, *g_W2, *g_W3, *g_b3;
     double *loss_acc;
+    long long max_samples;                  // records per step (0 = all)
+    const unsigned long long *step;         // Adam step count before this step
+    unsigned long long *used;               // records this step used
     int *err;
 };
 
@@ -178,7 +181,17 @@ __global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
     TTile t{tb, tb + kTX, tb + kTX + kTH, tb + kTX + 2 * kTH, tb + kTX + 2 * kTH + kTG, wimg, &mbar[tl],
             tb0, tb0 + 64, tb0 + 128, tb0 + 192, 0u, 1 + tl};
 
-    const long long nrec = (long long)min((unsigned long long)a.rec_cap, *a.rec_ctr);
+    // the records this step uses: all of them, or the stratum o, o + k, ...
+    // of about max_samples records (k = ceil(n / max_samples), o from the
+    // Adam step count)
+    const long long nall = (long long)min((unsigned long long)a.rec_cap, *a.rec_ctr);
+    long long kstride = 1, off = 0, nrec = nall;
+    if (a.max_samples > 0 && nall > a.max_samples) {
+        kstride = (nall + a.max_samples - 1) / a.max_samples;
+        off = (long long)((*a.step * 2654435761ull) % (unsigned long long)kstride);
+        nrec = (nall - off + kstride - 1) / kstride;
+    }
+    if (blockIdx.x == 0 && tid == 0) *a.used = (unsigned long long)nrec;
     const float inv_n = nrec > 0 ? 1.f / (float)nrec : 0.f;
     const long long ntiles = (nrec + 127) / 128;
     const size_t T = (size_t)1 << a.f.log2T;
@@ -187,8 +200,8 @@ __global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
     double loss_local = 0.0;
 
     for (long long tile = (long long)blockIdx.x * 2 + tl; tile < ntiles && ok; tile += (long long)gridDim.x * 2) {
-        const long long ri = tile * 128 + row;
-        const bool valid = ri < nrec;
+        const long long ri = off + (tile * 128 + row) * kstride;
+        const bool valid = tile * 128 + row < nrec;
         float rec[12];
         if (valid) {
             const float4 *p = reinterpret_cast<const float4 *>(a.rec + ri * 12);
@@ -426,6 +439,9 @@ wost_status train_grad_launch(wost_field *f, int dim, cudaStream_t st) {
     a.g_W3 = a.g_W2 + kHid * kHid;
     a.g_b3 = a.g_W3 + (size_t)f->nout * kHid;
     a.loss_acc = reinterpret_cast<double *>(f->loss_acc);
+    a.max_samples = f->t_samples;
+    a.step = f->adam_step();
+    a.used = f->used_records();
     a.err = device_err_flag();
     // one CTA per SM: each CTA holds all 512 TMEM columns of its SM
     wost_status rc = train_prepare(dim);

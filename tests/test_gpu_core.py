@@ -415,6 +415,47 @@ def test_train_gradient_parity(api, dim, kind):
             assert cos > 0.998 and rel < 6e-2, (name, cos, rel)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_train_step_on_a_strided_subset(api, dim):
+    # a training step of about m records takes the stratum o, o + k, ... of
+    # the buffer (k = ceil(n / m), o = t * 2654435761 mod k with t the Adam
+    # step count): the same loss and gradients as the explicit slice
+    sc = wi.half_disk(48, 12) if dim == 2 else wi.slab_box(2)
+    F, OF, fp = _field_pair(api, dim, 8, sc, w_scale=0.5, positive=True)
+    O = oracle.Scene(sc)
+    pts = _interior(sc, 96, 9, margin=0.05)
+    r = oracle.solve(O, oracle.make_params(eps=1e-3, maxsteps=256, seed=4, guided=1), pts, 0, 1, field=OF,
+                     records=True)
+    recs = r["records"].astype(np.float32)
+    n = len(recs)
+    m = n // 5 + 3
+    k = -(-n // m)
+    assert k >= 2
+    G = api.Field(dim, *sc.padded_bbox())
+
+    def check(off):
+        l_sub, g_sub = F.train_grad(samples=m)
+        p = F.get_params()
+        G.set_params(p["grid"], p["W1"], p["W2"], p["W3"], p["b3"])
+        G.set_records(recs[off::k])
+        l_ref, g_ref = G.train_grad()
+        assert l_sub == pytest.approx(l_ref, rel=1e-5)
+        for name in g_ref:
+            a, b = g_sub[name].ravel(), g_ref[name].ravel()
+            assert np.allclose(a, b, rtol=1e-4, atol=1e-6 * np.abs(b).max()), name
+        return l_ref, g_ref
+
+    F.set_records(recs)
+    l0, g0 = check(0)
+    ol, og, _ = OF.train_loss(recs[0::k].astype(np.float64))
+    assert l0 == pytest.approx(ol, rel=2e-2)
+    gv, ov = g0["W3"].astype(np.float64).ravel(), og[3].ravel()
+    assert gv @ ov / (np.linalg.norm(gv) * np.linalg.norm(ov)) > 0.9999
+    # one Adam step on the subset moves the stratum to o = 2654435761 mod k
+    F.train_step(exec_=api.exec_defaults(train_samples=m))
+    check(2654435761 % k)
+
+
 def test_online_training_runs_and_stays_unbiased(api):
     sc = wi.half_disk(48, 12)
     S = api.Scene(sc)
