@@ -411,6 +411,13 @@ WORKLOADS = {
                               "256x256 slice z = 0 masked inside, 64 walks/point, online training after every batch, "
                               "16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 MLP, K = 8",
                      grid=256, spp=64, eps=1e-3, maxsteps=128, l2="flushed (512 MiB write) before each step"),
+    "genus3": dict(workload="3D mixed Dirichlet/Neumann Laplace guided WoSt with learned MIS selection: genus-3 "
+                            "solid (sphere displaced by 0.15 Perlin noise minus three smoothly rimmed tunnels, "
+                            "993,640 triangles by surface nets), 30% Neumann cap, g = 1/|x - c|, 1024x1024 slice "
+                            "z = 0 masked inside, 128 walks/point, online training after every batch on 2^18 "
+                            "records, 16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 MLP, K = 8",
+                   grid=1024, spp=128, eps=1e-3, maxsteps=128, train_samples=1 << 18,
+                   l2="inputs larger than L2 (the BVHs and 1 M-walk batches); no flush"),
     "batch64": dict(workload="64 independent 2D star scenes (256-16384 segments log-uniform, Neumann fraction "
                              "U(0.2, 0.5), 1k-256k points and 8-128 walks per point log-uniform), one persistent "
                              "launch per training round under a CUDA graph, guided with online training per scene "
@@ -421,7 +428,7 @@ WORKLOADS = {
 
 def run_workload(args):
     """Other workloads of the method (same metric and timing rules), for the
-    design notes: --workload sphere3d | batch64 on one GPU."""
+    design notes: --workload sphere3d | genus3 | batch64 on one GPU."""
     import torch
     import wost_inputs as wi
     from paper_2410_18944_gb300 import api, build
@@ -431,8 +438,11 @@ def run_workload(args):
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     extra = {}
-    if args.workload == "sphere3d":
-        sc, pts_np = wi.config_3d_guided(res=W["grid"])
+    if args.workload in ("sphere3d", "genus3"):
+        if args.workload == "sphere3d":
+            sc, pts_np = wi.config_3d_guided(res=W["grid"])
+        else:
+            sc, pts_np = wi.config_genus3(res=W["grid"])
         S = api.Scene(sc)
         lo, hi = S.bbox()
         F = api.Field(3, lo, hi, seed=1)
@@ -446,7 +456,8 @@ def run_workload(args):
             torch.cuda.synchronize()
             ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             ev[0].record(stream)
-            kw = dict(guided=True, field=F, train=1, train_until_wpp=256) if guided else {}
+            kw = dict(guided=True, field=F, train=1, train_until_wpp=256,
+                      train_samples=W.get("train_samples", 0)) if guided else {}
             m, v, st = api.solve(S, pts, W["spp"], eps=W["eps"], maxsteps=W["maxsteps"], seed=i, stream=stream, **kw)
             ev[1].record(stream)
             torch.cuda.synchronize()
@@ -497,18 +508,27 @@ def run_workload(args):
 
 
 def run_once(args):
-    """One solve of (a seeded subset of) the workload, for profilers: no
-    timing loop, no oracle.  --once plain|guided, --points N, --spp S."""
+    """One solve of (a seeded subset of) a workload, for profilers: no
+    timing loop, no oracle.  --once plain|guided, --points N, --spp S,
+    --workload star2d|sphere3d|genus3."""
     import torch
     import wost_inputs as wi
     from paper_2410_18944_gb300 import api, build
     build.build()
-    sc, pts = make_workload()
+    dim = 2
+    if args.workload == "sphere3d":
+        sc, pts = wi.config_3d_guided(res=WORKLOADS["sphere3d"]["grid"])
+        dim = 3
+    elif args.workload == "genus3":
+        sc, pts = wi.config_genus3(res=WORKLOADS["genus3"]["grid"])
+        dim = 3
+    else:
+        sc, pts = make_workload()
     if args.points and args.points < len(pts):
         pts = wi.subsample(pts, args.points, seed=1)
     S = api.Scene(sc)
     lo, hi = S.bbox()
-    F = api.Field(2, lo, hi)
+    F = api.Field(dim, lo, hi)
     p = torch.tensor(pts, dtype=torch.float64, device="cuda")
     guided = args.once == "guided"
     for rep in range(2):

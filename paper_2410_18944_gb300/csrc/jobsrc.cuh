@@ -14,7 +14,18 @@
 // same problem solved alone.
 #pragma once
 #include "field.cuh"
+#include "lanewalk.cuh"
 #include "walkstep.cuh"
+
+// plain walks in 3D: 1 = per-lane query state machine (lanewalk.cuh), 0 =
+// one warp-synchronous query at a time (plain_loop below).  Measured on
+// one GB300 the state machine is 8-11% faster on the 3D workloads (82k and
+// 994k triangles) and 26% slower in 2D (4096 segments), where its larger
+// register footprint costs more occupancy than its convergence gains; both
+// give identical results.
+#ifndef WOST_PLAIN_LANES
+#define WOST_PLAIN_LANES 1
+#endif
 
 namespace wost {
 
@@ -186,6 +197,10 @@ struct BatchSrc {
 // ---------------------------------------------------------------------------
 template <int D, class Src>
 __device__ __forceinline__ void plain_loop(const Src &src, unsigned long long *stat) {
+    if (WOST_PLAIN_LANES && D == 3) {
+        plain_loop_lanes<D>(src, stat);
+        return;
+    }
     Walk<D> w;
     Visits vis;
     bool active = false, exhausted = false;

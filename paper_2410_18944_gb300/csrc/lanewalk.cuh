@@ -1,0 +1,327 @@
+// Plain walk loop as a per-lane state machine over the three boundary
+// queries of a walk-on-stars step (Sec. 3.2): closest Dirichlet point,
+// closest silhouette, first Neumann exit along a ray (source visibility and
+// the step itself).
+//
+// The query functions of geom.cuh run one query for the whole warp: the
+// warp leaves a query only when its slowest lane has finished it, so on
+// incoherent walks most lanes sit idle through the tail of every query.
+// Here every lane carries its own query (kind, BVH cursor, stack, best
+// result) through one loop:
+//   logic phase  - lanes whose query finished take the step logic that
+//                  follows it and set up their next query (or end the walk
+//                  and fetch the next one);
+//   node phase   - lanes at an inner node visit it, until every lane that
+//                  is still searching holds a leaf (while-while);
+//   leaf phase   - lanes at a leaf test its primitives.
+// A lane that finishes its query early starts its next one at the next
+// logic phase instead of waiting for the rest of the warp; over many walks
+// per lane the lanes' total work evens out.  Results are those of the
+// warp-synchronous queries: each query returns the minimum (distance or hit
+// parameter, ties to the smaller primitive id), which does not depend on the
+// order of visits.
+#pragma once
+#include "walkstep.cuh"
+
+namespace wost {
+
+enum : int { kQNone = 0, kQDir = 1, kQSil = 2, kQSrc = 3, kQMove = 4 };
+
+template <int D>
+struct LaneQuery {
+    int q = kQNone;   // query kind
+    bool fin = true;  // traversal finished: result in best / slot
+    int ref = 0, sp = 0;
+    float best = 0.f; // squared distance (Dirichlet, silhouette) or hit parameter (rays)
+    int slot = -1, id = 0x7fffffff;
+    float v[D], inv[D];
+    int stack[kStack];
+    float key[kStack];
+};
+
+template <int D>
+__device__ __forceinline__ const DevBVH &query_bvh(const DevScene &sc, int q) {
+    return q == kQDir ? sc.dir : (q == kQSil ? sc.sil : sc.neu);
+}
+
+// start a traversal of kind q from the root with initial bound best0
+template <int D>
+__device__ __forceinline__ void query_begin(LaneQuery<D> &Q, const DevScene &sc, int q, float best0) {
+    Q.q = q;
+    Q.ref = 0;
+    Q.sp = 0;
+    Q.best = best0;
+    Q.slot = -1;
+    Q.id = 0x7fffffff;
+    Q.fin = query_bvh<D>(sc, q).nprims == 0;
+}
+
+template <int D>
+__device__ __forceinline__ void query_ray(LaneQuery<D> &Q, const DevScene &sc, int q, const float *v, float tmax) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        Q.v[k] = v[k];
+        Q.inv[k] = 1.f / v[k];
+    }
+    query_begin<D>(Q, sc, q, tmax);
+}
+
+template <int D>
+__device__ __forceinline__ void query_pop(LaneQuery<D> &Q) {
+    while (Q.sp > 0) {
+        --Q.sp;
+        if (Q.key[Q.sp] <= Q.best) {
+            Q.ref = Q.stack[Q.sp];
+            return;
+        }
+    }
+    Q.fin = true;
+}
+
+// one inner node: order and keep the children within the bound
+template <int D>
+__device__ __forceinline__ void query_node(LaneQuery<D> &Q, const DevScene &sc, const float *x, float tneg,
+                                           int *err, Visits &vis) {
+    const DevBVH &bv = query_bvh<D>(sc, Q.q);
+    float k0, k1;
+    int r0, r1;
+    if (Q.q == kQDir || Q.q == kQSil) node_box_d2<D>(bv.nodes, Q.ref, x, k0, k1, r0, r1);
+    else node_box_ray<D>(bv.nodes, Q.ref, x, Q.inv, Q.best, k0, k1, r0, r1, tneg);
+    vis.nodes++;
+    bool h0 = k0 <= Q.best, h1 = k1 <= Q.best;
+    if (Q.q == kQSil && sc.sil_cones && (h0 || h1)) {
+        float lo0[3], hi0[3], lo1[3], hi1[3];
+        child_boxes<D>(bv.nodes, Q.ref, lo0, hi0, lo1, hi1);
+        if (h0 && cone_prunes<D>(ldn(sc.sil_cones + 2 * Q.ref), lo0, hi0, x, k0, sc.tau)) h0 = false;
+        if (h1 && cone_prunes<D>(ldn(sc.sil_cones + 2 * Q.ref + 1), lo1, hi1, x, k1, sc.tau)) h1 = false;
+    }
+    if (h0 && h1) {
+        const bool first0 = k0 <= k1;
+        if (Q.sp < kStack) {
+            Q.stack[Q.sp] = first0 ? r1 : r0;
+            Q.key[Q.sp] = first0 ? k1 : k0;
+            ++Q.sp;
+        } else {
+            atomicOr(err, 1);
+        }
+        Q.ref = first0 ? r0 : r1;
+    } else if (h0) {
+        Q.ref = r0;
+    } else if (h1) {
+        Q.ref = r1;
+    } else {
+        query_pop<D>(Q);
+    }
+}
+
+// one leaf: test its primitives, then continue from the stack
+template <int D>
+__device__ __forceinline__ void query_leaf(LaneQuery<D> &Q, const DevScene &sc, const float *x, int skip,
+                                           float tneg, Visits &vis) {
+    const int s0 = leaf_start(Q.ref), cnt = leaf_count(Q.ref);
+    if (Q.q == kQDir) {
+        const DevBVH &bv = sc.dir;
+        vis.dprims += cnt;
+        for (int s = s0; s < s0 + cnt; ++s) {
+            float d2;
+            if (D == 2) {
+                float4 p = __ldg(bv.prims + s);
+                float qx, qy;
+                d2 = seg_d2<float>(p.x, p.y, p.z, p.w, x[0], x[1], qx, qy);
+            } else {
+                float a[3], b[3], c[3], q[3];
+                load_tri(bv.prims, s, a, b, c);
+                d2 = tri_d2<float>(a, b, c, x, q);
+            }
+            if (d2 <= Q.best) {
+                int id = __ldg(bv.ids + s);
+                if (d2 < Q.best || id < Q.id) { Q.best = d2; Q.slot = s; Q.id = id; }
+            }
+        }
+    } else if (Q.q == kQSil) {
+        const DevBVH &bv = sc.sil;
+        vis.sprims += cnt;
+        for (int s = s0; s < s0 + cnt; ++s) {
+            float d2, o0, o1;
+            bool always;
+            if (D == 2) {
+                float4 e0 = __ldg(bv.prims + 2 * s), e1 = __ldg(bv.prims + 2 * s + 1);
+                float rx = x[0] - e0.x, ry = x[1] - e0.y;
+                d2 = rx * rx + ry * ry;
+                o0 = e0.z * rx + e0.w * ry;
+                o1 = e1.x * rx + e1.y * ry;
+                always = e1.z != 0.f;
+            } else {
+                float4 e0 = __ldg(bv.prims + 4 * s), e1 = __ldg(bv.prims + 4 * s + 1);
+                float4 e2 = __ldg(bv.prims + 4 * s + 2), e3 = __ldg(bv.prims + 4 * s + 3);
+                float a[3] = {e0.x, e0.y, e0.z}, b[3] = {e0.w, e1.x, e1.y};
+                d2 = seg3_d2<float>(a, b, x);
+                float r[3] = {x[0] - a[0], x[1] - a[1], x[2] - a[2]};
+                o0 = e1.z * r[0] + e1.w * r[1] + e2.x * r[2];
+                o1 = e2.y * r[0] + e2.z * r[1] + e2.w * r[2];
+                always = e3.x != 0.f;
+            }
+            if (d2 <= Q.best && (always || sil_rule(o0, o1, sc.tau))) {
+                int id = __ldg(bv.ids + s);
+                if (d2 < Q.best || id < Q.id) { Q.best = d2; Q.slot = s; Q.id = id; }
+            }
+        }
+    } else {
+        const DevBVH &bv = sc.neu;
+        vis.nprims += cnt;
+        for (int s = s0; s < s0 + cnt; ++s) {
+            float t;
+            if (s != skip && ray_prim<D, true>(bv.prims, s, x, Q.v, t, tneg) && t <= Q.best) {
+                int id = __ldg(bv.ids + s);
+                if (t < Q.best || id < Q.id) { Q.best = t; Q.slot = s; Q.id = id; }
+            }
+        }
+    }
+    query_pop<D>(Q);
+}
+
+// The plain walk (uniform directions, reflection at Neumann points) over a
+// job source, step for step the computation of plain_loop: the same random
+// numbers, tests and updates in the same order per walk.
+template <int D, class Src>
+__device__ __forceinline__ void plain_loop_lanes(const Src &src, unsigned long long *stat) {
+    Walk<D> w;
+    w.job = 0;        // a lane without a walk still names a valid job
+    w.prim = -1;
+    LaneQuery<D> Q;
+    Visits vis;
+    bool active = false, exhausted = false;
+    unsigned long long nsteps = 0, ntrunc = 0, nwalks = 0;
+    float RD = 0.f, r = 0.f, rho = 0.f;
+    int dslot = -1;
+    const float kInf = __int_as_float(0x7f800000);
+    for (;;) {
+        // ---- logic phase ----
+        if (Q.fin && Q.q != kQNone) {
+            const StepEnv env = src.env(w);
+            const DevScene &sc = env.sc;
+            const float tneg = kRoundBand * sc.scale;
+            bool dir_move = false;   // draw the step direction and cast the step ray
+            if (Q.q == kQDir) {
+                float bd2 = Q.best;
+                dslot = Q.slot;
+                RD = sqrtf(bd2);
+                double q64[3];
+                bool have64 = false, shell;
+                if (fabsf(RD - env.eps) <= kRoundBand * (sc.scale + RD)) {
+                    shell = dirichlet_dist64<D>(sc.dir, dslot, w.x, q64) <= env.eps64;
+                    have64 = true;
+                } else {
+                    shell = RD <= env.eps;
+                }
+                if (shell || w.k >= env.maxsteps) {
+                    if (!have64) dirichlet_dist64<D>(sc.dir, dslot, w.x, q64);
+                    float xb[3] = {(float)q64[0], (float)q64[1], D == 3 ? (float)q64[2] : 0.f};
+                    w.acc += w.T * eval_fn<D>(sc.g, xb);
+                    src.finish(w);
+                    ntrunc += !shell;
+                    active = false;
+                    Q.q = kQNone;
+                } else {
+                    query_begin<D>(Q, sc, kQSil, RD * RD);
+                }
+            } else if (Q.q == kQSil) {
+                float R = fminf(sqrtf(Q.best), RD);
+                r = fmaxf(R, env.eps);
+                if (sc.has_source) {
+                    U4 u = philox(w.pid, w.wid, (uint32_t)w.k, P_SRC, env.key0, env.key1);
+                    float vs[D];
+                    uniform_dir<D>(u01(u.x), u01(u.y), vs);
+                    if (w.prim >= 0 && dotv<D>(vs, w.n) < 0.f) reflect<D>(vs, w.n);
+                    rho = D == 2 ? r * sqrtf(u01(u.z) * u01(u.w)) : r * beta22_inv(u01(u.z));
+                    query_ray<D>(Q, sc, kQSrc, vs, rho);
+                } else {
+                    dir_move = true;
+                }
+            } else if (Q.q == kQSrc) {
+                int hs = Q.slot;
+                const float th = Q.best;
+                if (hs >= 0 && rho - th <= kRoundBand * (sc.scale + rho)) {
+                    double t64;
+                    if (!ray_prim64<D, true>(sc.neu, hs, w.x, Q.v, t64, tneg) || t64 > (double)rho) hs = -1;
+                }
+                float S = 0.f;
+                if (hs < 0) {
+                    float y[3];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) y[i] = w.x[i] + rho * Q.v[i];
+                    S = -(r * r / (2.f * D)) * eval_fn<D>(sc.f, y);
+                }
+                w.acc += w.T * S;
+                dir_move = true;
+            } else if (Q.q == kQMove) {
+                int hit = Q.slot;
+                float th = Q.best;
+                if (hit >= 0 && r - th <= kRoundBand * (sc.scale + r)) {
+                    double t64;
+                    if (!ray_prim64<D, true>(sc.neu, hit, w.x, Q.v, t64, tneg) || t64 > (double)r) hit = -1;
+                }
+                if (hit >= 0) {
+                    // exit hit: stand tneg inside along the primitive's inward normal
+                    th = fmaxf(th, 0.f);
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        w.n[i] = __ldg(sc.nin_neu + (size_t)hit * D + i);
+                        w.x[i] += th * Q.v[i] + tneg * w.n[i];
+                    }
+                    w.prim = hit;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) w.x[i] += r * Q.v[i];
+                    w.prim = -1;
+                }
+                w.k++;
+                nsteps++;
+                query_begin<D>(Q, sc, kQDir, kInf);
+            }
+            if (dir_move) {
+                U4 u = philox(w.pid, w.wid, (uint32_t)w.k, P_DIR, env.key0, env.key1);
+                float nu[D];
+                uniform_dir<D>(u01(u.x), u01(u.y), nu);
+                bool ended = false;
+                if (w.prim >= 0) {
+                    float dn = dotv<D>(nu, w.n);
+                    if (dn < 0.f) reflect<D>(nu, w.n);
+                    ended = dn == 0.f;   // zero density at the tangent plane (Eq. angular_req)
+                }
+                if (ended) {
+                    src.finish(w);
+                    active = false;
+                    Q.q = kQNone;
+                } else {
+                    query_ray<D>(Q, sc, kQMove, nu, r);
+                }
+            }
+        }
+        if (!active && !exhausted) {
+            unsigned long long item = warp_fetch_add(src.work_ctr(), true);
+            if (item >= src.total()) {
+                exhausted = true;
+            } else if (src.start(w, item)) {
+                active = true;
+                nwalks++;
+                nsteps++;
+                query_begin<D>(Q, src.env(w).sc, kQDir, kInf);
+            }
+        }
+        if (!__any_sync(0xffffffffu, active || !exhausted)) break;
+        __syncwarp();
+        const bool searching = active && !Q.fin;
+        if (!__any_sync(0xffffffffu, searching)) continue;
+        // ---- node and leaf phases ----
+        const StepEnv env = src.env(w);
+        const float tneg = kRoundBand * env.sc.scale;
+        while (__any_sync(0xffffffffu, searching && !Q.fin && Q.ref >= 0)) {
+            if (searching && !Q.fin && Q.ref >= 0) query_node<D>(Q, env.sc, w.x, tneg, env.err, vis);
+        }
+        if (searching && !Q.fin) query_leaf<D>(Q, env.sc, w.x, w.prim, tneg, vis);
+    }
+    flush_stats(stat, nsteps, ntrunc, nwalks, vis);
+}
+
+}  // namespace wost
