@@ -97,7 +97,7 @@ __device__ __forceinline__ float eval_fn(const DevFn &fn, const float *x) {
 // ---------------------------------------------------------------------------
 struct DevBVH {
     const float4 *nodes;  // global memory, or shared memory when a kernel staged them
-    const float4 *prims;
+    const float4 *prims;  // (likewise)
     const int *ids;       // original primitive / element id per leaf slot
     const double *prims64; // FP64 copy of the primitive vertices (leaf order), 2D: 4, 3D: 9 doubles
     int nprims;
@@ -115,8 +115,8 @@ struct DevScene {
     int has_source;
 };
 
-// node and normal-cone loads: generic, as the arrays may have been staged in
-// shared memory by the kernel
+// BVH node, normal-cone and primitive loads: generic, as the arrays may
+// have been staged in shared memory by the kernel
 __device__ __forceinline__ float4 ldn(const float4 *p) { return *p; }
 
 __device__ __forceinline__ int leaf_start(int ref) { return (~ref) >> 4; }

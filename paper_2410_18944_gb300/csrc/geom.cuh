@@ -145,7 +145,7 @@ __device__ __forceinline__ R tri_d2(const R *a, const R *b, const R *c, const R 
 }
 
 __device__ __forceinline__ void load_tri(const float4 *__restrict__ P, int s, float *a, float *b, float *c) {
-    float4 u = __ldg(P + 3 * s), v = __ldg(P + 3 * s + 1), w = __ldg(P + 3 * s + 2);
+    float4 u = ldn(P + 3 * s), v = ldn(P + 3 * s + 1), w = ldn(P + 3 * s + 2);
     a[0] = u.x; a[1] = u.y; a[2] = u.z; b[0] = u.w; b[1] = v.x; b[2] = v.y; c[0] = v.z; c[1] = v.w; c[2] = w.x;
 }
 
@@ -209,7 +209,7 @@ __device__ int closest_dirichlet(const DevBVH &bv, const float *x, float &best, 
             for (int s = s0; s < s0 + cnt; ++s) {
                 float d2;
                 if (D == 2) {
-                    float4 p = __ldg(bv.prims + s);
+                    float4 p = ldn(bv.prims + s);
                     float qx, qy;
                     d2 = seg_d2<float>(p.x, p.y, p.z, p.w, x[0], x[1], qx, qy);
                 } else {
@@ -345,15 +345,15 @@ __device__ int closest_silhouette(const DevBVH &bv, const float *x, float tau, f
                 float d2, o0, o1;
                 bool always;
                 if (D == 2) {
-                    float4 e0 = __ldg(bv.prims + 2 * s), e1 = __ldg(bv.prims + 2 * s + 1);
+                    float4 e0 = ldn(bv.prims + 2 * s), e1 = ldn(bv.prims + 2 * s + 1);
                     float rx = x[0] - e0.x, ry = x[1] - e0.y;
                     d2 = rx * rx + ry * ry;
                     o0 = e0.z * rx + e0.w * ry;
                     o1 = e1.x * rx + e1.y * ry;
                     always = e1.z != 0.f;
                 } else {
-                    float4 e0 = __ldg(bv.prims + 4 * s), e1 = __ldg(bv.prims + 4 * s + 1);
-                    float4 e2 = __ldg(bv.prims + 4 * s + 2), e3 = __ldg(bv.prims + 4 * s + 3);
+                    float4 e0 = ldn(bv.prims + 4 * s), e1 = ldn(bv.prims + 4 * s + 1);
+                    float4 e2 = ldn(bv.prims + 4 * s + 2), e3 = ldn(bv.prims + 4 * s + 3);
                     float a[3] = {e0.x, e0.y, e0.z}, b[3] = {e0.w, e1.x, e1.y};
                     d2 = seg3_d2<float>(a, b, x);
                     float r[3] = {x[0] - a[0], x[1] - a[1], x[2] - a[2]};
@@ -391,7 +391,7 @@ template <int D, bool kExit = false>
 __device__ __forceinline__ bool ray_prim(const float4 *__restrict__ P, int s, const float *o, const float *v, float &t,
                                          float tneg = 0.f) {
     if (D == 2) {
-        float4 p = __ldg(P + s);
+        float4 p = ldn(P + s);
         float ex = p.z - p.x, ey = p.w - p.y;
         float ax = p.x - o[0], ay = p.y - o[1];
         float den = v[0] * ey - v[1] * ex;

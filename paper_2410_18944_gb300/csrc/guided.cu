@@ -18,7 +18,7 @@ struct GuidedArgs {
     DevField f;
     WsOpts o;
     RecDest rd;
-    int stage_f4;      // float4 of BVH nodes / cones staged in shared memory (0: none)
+    int stage_mask;    // scene regions staged in shared memory (stage_plan)
 };
 
 template <int D>
@@ -26,8 +26,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) guided_walk_kernel(const __grid
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ DevScene staged;
     const DevScene *sc = &g.w.sc;
-    if (g.stage_f4 > 0) {
-        stage_scene(g.w.sc, staged, reinterpret_cast<float4 *>(sm + kWsSmem));
+    if (g.stage_mask) {
+        stage_scene(g.w.sc, staged, reinterpret_cast<float4 *>(sm + kWsSmem), g.stage_mask);
         sc = &staged;
     }
     guided_ws_body<D, false>(SoloSrc<D>{g.w, &g.f, g.rd, sc}, g.o, sm);
@@ -102,15 +102,34 @@ wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_ada
 
 int guided_ctas_per_sm() { return 1; }
 
-// the warp-specialised walk kernel runs one CTA (512 threads) per SM; its
-// dynamic shared memory holds the decode tiles and, when they fit, the
-// scene's BVH nodes and cones
-constexpr int kStageMaxBytes = 96 * 1024;
+// The warp-specialised walk kernel runs one CTA (512 threads) per SM; its
+// dynamic shared memory holds the decode tiles and as much of the scene's
+// traversal data as fits (stage_plan), at most WOST_STAGE_MAX_KB.
+#ifndef WOST_STAGE_MAX_KB
+#define WOST_STAGE_MAX_KB 1024
+#endif
+
+// bytes of dynamic shared memory beyond the tiles that a walk kernel may use
+static int stage_budget_bytes() {
+    static int budget = -1;
+    if (budget < 0) {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes f2{}, f3{};
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&f2, guided_walk_kernel<2>) != cudaSuccess ||
+            cudaFuncGetAttributes(&f3, guided_walk_kernel<3>) != cudaSuccess)
+            return 0;
+        const int stat = (int)std::max(f2.sharedSizeBytes, f3.sharedSizeBytes);
+        budget = std::max(0, std::min(optin - kWsSmem - stat - 1024, WOST_STAGE_MAX_KB * 1024));
+    }
+    return budget;
+}
 
 wost_status guided_occupancy(int dim, int *per_sm) {
     static bool set[4] = {false, false, false, false};
     if (!set[dim]) {
-        const int bytes = kWsSmem + kStageMaxBytes;
+        const int bytes = kWsSmem + stage_budget_bytes();
         if (dim == 2) WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         else WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         set[dim] = true;
@@ -119,13 +138,15 @@ wost_status guided_occupancy(int dim, int *per_sm) {
     return WOST_OK;
 }
 
-int stage_f4_for(const DevScene &sc) {
-    const int f4 = scene_node_f4(sc);
-    return f4 * 16 <= kStageMaxBytes ? f4 : 0;
+// regions of the scene to stage, and their size in float4
+static int stage_mask_for(const DevScene &sc, int *f4) {
+    return stage_plan(sc, stage_budget_bytes() / 16, f4);
 }
 
 wost_status launch_guided(int dim, const GuidedArgs &g, int grid, cudaStream_t st) {
-    const int smem = kWsSmem + g.stage_f4 * 16;
+    int f4 = 0;
+    stage_mask_for(g.w.sc, &f4);
+    const int smem = kWsSmem + f4 * 16;
     if (dim == 2) guided_walk_kernel<2><<<grid, kWsThreads, smem, st>>>(g);
     else guided_walk_kernel<3><<<grid, kWsThreads, smem, st>>>(g);
     WOST_CUDA(cudaGetLastError());
@@ -145,7 +166,10 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
     if (f->desc.dim != s->dim) { set_error("wost_solve: field dimension differs from the scene"); return WOST_ERR_INVALID_ARG; }
     GuidedArgs g{};
     g.f = f->dev();
-    g.stage_f4 = stage_f4_for(s->dev);
+    {
+        int f4 = 0;
+        g.stage_mask = stage_mask_for(s->dev, &f4);
+    }
     g.o.c_mode = ex.c_mode;
     g.o.c_fixed = ex.c_fixed;
     g.o.reflect = ex.reflect;

@@ -66,36 +66,70 @@ struct SoloSrc {
     __device__ __forceinline__ const float *b3(int) const { return f->b3; }
 };
 
-// Float4 count of a scene's BVH nodes and silhouette normal cones, the data
-// every traversal step reads first.
-__host__ __device__ __forceinline__ int scene_node_f4(const DevScene &s) {
-    const int nb = s.dim == 2 ? 3 : 4;
-    return (s.dir.nnodes + s.neu.nnodes + s.sil.nnodes) * nb + (s.sil_cones ? 2 * s.sil.nnodes : 0);
+// Staging of a scene's traversal data in shared memory.  A walk step is a
+// chain of dependent loads of BVH nodes and leaf primitives, so their
+// latency is the step's latency; a kernel with shared memory to spare keeps
+// as much of the data there as fits.  Regions, in the order they are taken:
+// the three BVHs' nodes, the silhouette normal cones, then the Dirichlet,
+// Neumann and silhouette primitives.
+constexpr int kStageRegions = 7;
+
+__host__ __device__ __forceinline__ void stage_regions(const DevScene &s, const float4 **src, int *cnt) {
+    const int nb = s.dim == 2 ? 3 : 4;       // float4 per node
+    const int pd = s.dim == 2 ? 1 : 3;       // per Dirichlet / Neumann primitive
+    const int ps = s.dim == 2 ? 2 : 4;       // per silhouette element
+    src[0] = s.dir.nodes; cnt[0] = s.dir.nnodes * nb;
+    src[1] = s.neu.nodes; cnt[1] = s.neu.nnodes * nb;
+    src[2] = s.sil.nodes; cnt[2] = s.sil.nnodes * nb;
+    src[3] = s.sil_cones; cnt[3] = s.sil_cones ? 2 * s.sil.nnodes : 0;
+    src[4] = s.dir.prims; cnt[4] = s.dir.nprims * pd;
+    src[5] = s.neu.prims; cnt[5] = s.neu.nprims * pd;
+    src[6] = s.sil.prims; cnt[6] = s.sil.nprims * ps;
 }
 
-// Copies the BVH nodes and cones of `in` into shared memory `dst` (all
-// threads of the block take part) and makes `out` (shared) a copy of the
-// scene view pointing at them.  Traversal node loads then come from shared
-// memory: a walk step is a chain of dependent node loads, so their latency
-// is the step's latency.
-__device__ __forceinline__ void stage_scene(const DevScene &in, DevScene &out, float4 *dst) {
-    const int nb = in.dim == 2 ? 3 : 4;
-    const float4 *src[4] = {in.dir.nodes, in.neu.nodes, in.sil.nodes, in.sil_cones};
-    const int cnt[4] = {in.dir.nnodes * nb, in.neu.nnodes * nb, in.sil.nnodes * nb, in.sil_cones ? 2 * in.sil.nnodes : 0};
-    float4 *start[4];
+// Which regions fit in budget_f4 float4 (bit r = region r), greedily in
+// order: all node regions or none, then whole primitive arrays.
+__host__ __forceinline__ int stage_plan(const DevScene &s, int budget_f4, int *total_f4) {
+    const float4 *src[kStageRegions];
+    int cnt[kStageRegions];
+    stage_regions(s, src, cnt);
+    int mask = 0, used = 0;
+    const int nodes = cnt[0] + cnt[1] + cnt[2] + cnt[3];
+    if (nodes <= budget_f4) {
+        mask = 0xF;
+        used = nodes;
+        for (int r = 4; r < kStageRegions; ++r)
+            if (cnt[r] > 0 && used + cnt[r] <= budget_f4) { mask |= 1 << r; used += cnt[r]; }
+    }
+    *total_f4 = used;
+    return mask;
+}
+
+// Copies the regions in `mask` into shared memory `dst` (all threads of the
+// block take part) and makes `out` (shared) a copy of the scene view whose
+// pointers name the staged copies.
+__device__ __forceinline__ void stage_scene(const DevScene &in, DevScene &out, float4 *dst, int mask) {
+    const float4 *src[kStageRegions];
+    int cnt[kStageRegions];
+    stage_regions(in, src, cnt);
+    float4 *start[kStageRegions];
     float4 *d = dst;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < kStageRegions; ++r) {
         start[r] = d;
+        if (!(mask >> r & 1) || cnt[r] == 0) continue;
         for (int i = threadIdx.x; i < cnt[r]; i += blockDim.x) d[i] = __ldg(src[r] + i);
         d += cnt[r];
     }
     if (threadIdx.x == 0) {
         out = in;
-        if (cnt[0]) out.dir.nodes = start[0];
-        if (cnt[1]) out.neu.nodes = start[1];
-        if (cnt[2]) out.sil.nodes = start[2];
-        if (cnt[3]) out.sil_cones = start[3];
+        auto take = [&](int r) { return (mask >> r & 1) && cnt[r] > 0; };
+        if (take(0)) out.dir.nodes = start[0];
+        if (take(1)) out.neu.nodes = start[1];
+        if (take(2)) out.sil.nodes = start[2];
+        if (take(3)) out.sil_cones = start[3];
+        if (take(4)) out.dir.prims = start[4];
+        if (take(5)) out.neu.prims = start[5];
+        if (take(6)) out.sil.prims = start[6];
     }
     __syncthreads();
 }

@@ -125,7 +125,7 @@ __device__ __forceinline__ void query_leaf(LaneQuery<D> &Q, const DevScene &sc, 
         for (int s = s0; s < s0 + cnt; ++s) {
             float d2;
             if (D == 2) {
-                float4 p = __ldg(bv.prims + s);
+                float4 p = ldn(bv.prims + s);
                 float qx, qy;
                 d2 = seg_d2<float>(p.x, p.y, p.z, p.w, x[0], x[1], qx, qy);
             } else {
@@ -145,15 +145,15 @@ __device__ __forceinline__ void query_leaf(LaneQuery<D> &Q, const DevScene &sc, 
             float d2, o0, o1;
             bool always;
             if (D == 2) {
-                float4 e0 = __ldg(bv.prims + 2 * s), e1 = __ldg(bv.prims + 2 * s + 1);
+                float4 e0 = ldn(bv.prims + 2 * s), e1 = ldn(bv.prims + 2 * s + 1);
                 float rx = x[0] - e0.x, ry = x[1] - e0.y;
                 d2 = rx * rx + ry * ry;
                 o0 = e0.z * rx + e0.w * ry;
                 o1 = e1.x * rx + e1.y * ry;
                 always = e1.z != 0.f;
             } else {
-                float4 e0 = __ldg(bv.prims + 4 * s), e1 = __ldg(bv.prims + 4 * s + 1);
-                float4 e2 = __ldg(bv.prims + 4 * s + 2), e3 = __ldg(bv.prims + 4 * s + 3);
+                float4 e0 = ldn(bv.prims + 4 * s), e1 = ldn(bv.prims + 4 * s + 1);
+                float4 e2 = ldn(bv.prims + 4 * s + 2), e3 = ldn(bv.prims + 4 * s + 3);
                 float a[3] = {e0.x, e0.y, e0.z}, b[3] = {e0.w, e1.x, e1.y};
                 d2 = seg3_d2<float>(a, b, x);
                 float r[3] = {x[0] - a[0], x[1] - a[1], x[2] - a[2]};

@@ -358,19 +358,23 @@ def test_guided_c_zero_equals_plain(api):
     assert sg["walk_steps"] == sp["walk_steps"]
 
 
-@pytest.mark.parametrize("dim", [2, 3])
-def test_guided_frozen_field_vs_closed_form_and_oracle(api, dim):
+@pytest.mark.parametrize("dim,reflect", [(2, 1), (3, 1), (2, 0), (3, 0)])
+def test_guided_frozen_field_vs_closed_form_and_oracle(api, dim, reflect):
+    # reflect = 0: guided samples below the tangent plane at a Neumann point
+    # are not reflected and end the walk's recursion (zero density), the
+    # ablation of Sec. 4.3; still unbiased
     sc = wi.half_disk(48, 12) if dim == 2 else wi.slab_box(2)
     S, O = api.Scene(sc), oracle.Scene(sc)
     F, OF, _ = _field_pair(api, dim, 6, sc, w_scale=1.5)
     pts = _interior(sc, 24, 6)
     n = 8192 if dim == 2 else 4096
-    m, v, st = api.solve(S, pts, n, eps=1e-3, maxsteps=1024, seed=7, guided=True, field=F)
+    m, v, st = api.solve(S, pts, n, eps=1e-3, maxsteps=1024, seed=7, guided=True, field=F, reflect=reflect)
     ex = wi.eval_fn(sc.exact, pts)
     z = (m - ex) / np.sqrt(v)
     assert np.all(np.abs(z) < 4.5), z
     no = 1024
-    r = oracle.solve(O, oracle.make_params(eps=1e-3, maxsteps=1024, seed=7, guided=1), pts, 0, no, field=OF)
+    r = oracle.solve(O, oracle.make_params(eps=1e-3, maxsteps=1024, seed=7, guided=1, reflect=reflect), pts, 0, no,
+                     field=OF)
     om, ov = oracle.mean_var(r["sum"], r["sum2"], no)
     zo = (m - om) / np.sqrt(v + ov)
     assert np.all(np.abs(zo) < 4.5), zo

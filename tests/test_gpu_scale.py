@@ -11,8 +11,9 @@
   against plain;
 * the 4096-segment star with the benchmark's guided solve (online training
   after every batch of one walk per point, 32 walks per point) against a
-  high-sample plain reference at every one of its 174,115 points: online
-  training changes the sampler, never the expectation."""
+  high-sample plain reference at its 174,115 points, held to a plain solve of
+  the same size: online training changes the sampler, never the
+  expectation."""
 import numpy as np
 import pytest
 
@@ -95,14 +96,30 @@ def test_star_benchmark_solve_is_unbiased_everywhere(api):
     m, v, st = api.solve(S, pd, 32, eps=1e-3, maxsteps=128, seed=11, guided=True, field=F, train=1,
                          train_until_wpp=256)
     assert st["train_steps"] == 32 and st["records_dropped"] == 0
+    mp, vp, _ = api.solve(S, pd, 32, eps=1e-3, maxsteps=128, seed=11)
     mr, vr, _ = api.solve(S, pd, 1024, eps=1e-3, maxsteps=128, seed=12)
-    m, v, mr, vr = (t.cpu().numpy() for t in (m, v, mr, vr))
+    m, v, mp, vp, mr, vr = (t.cpu().numpy() for t in (m, v, mp, vp, mr, vr))
     assert np.all(np.isfinite(m))
     shell = (v == 0) & (vr == 0)          # eps-shell points: g at the closest point, both sides
     assert shell.mean() < 0.01 and np.array_equal(m[shell], mr[shell])
-    z = (m - mr)[~shell] / np.sqrt(v + vr)[~shell]
-    assert np.mean(np.abs(z) < 4.5) > 0.9995, np.sort(np.abs(z))[-10:]
-    assert abs(np.mean(z)) < 0.02 and 0.9 < np.std(z) < 1.1, (np.mean(z), np.std(z))
+    # Near the Neumann arc the walk values are skewed (a few percent of the
+    # walks there reach the step cap and end at a distant Dirichlet point),
+    # so the sample variance of 32 walks runs small now and then and a few
+    # tenths of a percent of the per-point z-scores pass 4.5 for plain walks
+    # as well (measured: 0.36% at 32 walks, 3e-5 at 256, 6e-6 at 1024).  The
+    # guided solve is held to the plain solve of the same size, point by
+    # point, and to the reference over blocks of 256 points.
+    def zs(a, va):
+        return (a - mr)[~shell] / np.sqrt(va + vr)[~shell]
+    zg, zp = zs(m, v), zs(mp, vp)
+    bad_g, bad_p = np.mean(np.abs(zg) > 4.5), np.mean(np.abs(zp) > 4.5)
+    assert bad_g <= 2 * bad_p + 2e-4, (bad_g, bad_p)
+    assert abs(np.mean(zg) - np.mean(zp)) < 0.05 and np.std(zg) < 1.1 * np.std(zp), \
+        (np.mean(zg), np.mean(zp), np.std(zg), np.std(zp))
+    d, s2 = (m - mr)[~shell], (v + vr)[~shell]
+    nb = len(d) // 256
+    zb = d[:nb * 256].reshape(nb, 256).sum(1) / np.sqrt(s2[:nb * 256].reshape(nb, 256).sum(1))
+    assert np.all(np.abs(zb) < 5) and abs(np.mean(zb)) < 0.1, (np.sort(np.abs(zb))[-5:], np.mean(zb))
 
 
 @pytest.fixture(scope="module")
@@ -160,5 +177,8 @@ def test_genus3_mixed_vs_oracle_same_streams(api, genus3):
     mg, vg, _ = api.solve(S, pd, 4096, eps=1e-3, maxsteps=256, seed=12, guided=True, field=F)
     mp, vp, mg, vg = (t.cpu().numpy() for t in (mp, vp, mg, vg))
     assert np.all(np.isfinite(mg)) and np.all(np.abs((mg - mp) / np.sqrt(vg + vp)) < 4.5)
-    zo = (mp - om) / np.sqrt(vp + ov + 1e-30)
-    assert np.sum(zo[ov > 0] ** 2) < 3 * max(1, (ov > 0).sum()), zo
+    # the oracle's 8-walk mean against the 4096-walk solve; its variance is
+    # the per-walk variance the 4096 walks estimate, over 8 (the 8-walk
+    # sample variance is too noisy to scale a z-score)
+    zo = (mp - om) / np.sqrt(vp * (1 + 4096 / no))
+    assert np.sum(zo ** 2) < 45 and np.all(np.abs(zo) < 5), zo
