@@ -79,7 +79,10 @@ constexpr int ws_smem_bytes(bool multi) {
     return kWImgBytes * ws_weight_slots(multi) + kNT * kBufBytes + kWsCtrlBytes +
            (multi ? kNT * (128 * 4 + kYBytes) : 0);
 }
-constexpr uint32_t kFlushPolls = 256;        // server polls before closing a partial tile
+#ifndef WOST_FLUSH_POLLS
+#define WOST_FLUSH_POLLS 256
+#endif
+constexpr uint32_t kFlushPolls = WOST_FLUSH_POLLS;   // server polls before closing a partial tile
 // Decode in flight during the step's geometry.  Measured on the 2D star
 // workload it is slower (the terminal steps' decodes are wasted and tile
 // buffers stay held through the geometry), so it is off by default.
@@ -219,11 +222,16 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
                 for (;;) {
                     if (mbar_try_wait(&ctl->full[b], k & 1u)) { go = 1; break; }
                     if (globaltimer_ns() - t0 > kWaitNs) break;
-                    if (++polls < o.flush_polls) continue;
-                    polls = 0;
                     int q = *(volatile int *)&ctl->qclaim;
+                    const int alive = *(volatile int *)&ctl->alive;
+                    // every walker warp still running has claimed a quarter of
+                    // this tile: no further claim can come before it is
+                    // decoded, so close it now instead of after the poll budget
+                    const bool all_in = q > 4 * T && q - 4 * T >= alive;
+                    if (!all_in && ++polls < o.flush_polls) continue;
+                    polls = 0;
                     if (q <= 4 * T) {
-                        if (*(volatile int *)&ctl->alive == 0) { go = 0; break; }
+                        if (alive == 0) { go = 0; break; }
                     } else if (q < 4 * T + 4 && atomicCAS(&ctl->qclaim, q, 4 * T + 4) == q) {
                         // close the tile: zero-fill the unclaimed quarters and arrive for them
                         for (int qq = q - 4 * T; qq < 4; ++qq) {
