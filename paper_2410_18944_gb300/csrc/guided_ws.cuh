@@ -83,6 +83,11 @@ constexpr int ws_smem_bytes(bool multi) {
 #define WOST_FLUSH_POLLS 256
 #endif
 constexpr uint32_t kFlushPolls = WOST_FLUSH_POLLS;   // server polls before closing a partial tile
+// optional bound in time on the wait for a partial tile (0: polls only)
+#ifndef WOST_FLUSH_NS
+#define WOST_FLUSH_NS 0
+#endif
+constexpr unsigned long long kFlushNs = WOST_FLUSH_NS;
 // Decode in flight during the step's geometry.  Measured on the 2D star
 // workload it is slower (the terminal steps' decodes are wasted and tile
 // buffers stay held through the geometry), so it is off by default.
@@ -228,7 +233,8 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
                     // this tile: no further claim can come before it is
                     // decoded, so close it now instead of after the poll budget
                     const bool all_in = q > 4 * T && q - 4 * T >= alive;
-                    if (!all_in && ++polls < o.flush_polls) continue;
+                    const bool late = kFlushNs > 0 && globaltimer_ns() - t0 > kFlushNs;
+                    if (!all_in && !late && ++polls < o.flush_polls) continue;
                     polls = 0;
                     if (q <= 4 * T) {
                         if (alive == 0) { go = 0; break; }
