@@ -124,12 +124,14 @@ typedef struct {
                                   all draw the same random numbers */
     int32_t wavefront_slots;   /* walks in flight in a wavefront launch that trains nothing
                                   (0 = 2^20); a launch that trains holds one walk per point */
-    int64_t train_samples;     /* records per training step (Sec. 5.2, online training on
-                                  fixed-size batches): 0 = every record of the batch; otherwise,
-                                  with n records and n > train_samples, the step uses records
-                                  o, o + k, o + 2k, ... < n with k = ceil(n / train_samples) and
-                                  o = (t * 2654435761) mod k, t the field's Adam step count
-                                  before the step (so consecutive steps take different strata) */
+    int64_t train_samples;     /* records per training step (Sec. 5.2, online training in
+                                  minibatches): 0 = one step on every record of the batch.
+                                  Otherwise, with n > train_samples records, k = ceil(n /
+                                  train_samples): after each batch of wost_solve the field takes
+                                  k Adam steps, step j on records j, j + k, j + 2k, ... < n (every
+                                  record once); one wost_train_step / wost_train_grad call takes
+                                  the stratum o = (t * 2654435761) mod k, t the field's Adam step
+                                  count before the step */
 } wost_exec;
 
 typedef struct {

@@ -26,7 +26,8 @@
 
 namespace wost {
 
-wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *loss_out_dev);
+wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *loss_out_dev,
+                         long long off = -1);
 wost_status train_prepare(int dim);
 wost_status ensure_records(wost_field *f, int64_t cap, size_t scratch_bytes);
 

@@ -20,7 +20,8 @@ wost_status cuda_status(cudaError_t e, const char *what) {
 }
 
 wost_status refresh_inference_copy(wost_field *f, cudaStream_t st);
-wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *loss_out_dev);
+wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *loss_out_dev,
+                         long long off = -1);
 int *device_err_flag();
 wost_status device_check(cudaStream_t st);
 

@@ -98,7 +98,9 @@ __global__ void mixture_sample_kernel(int K, const float *mu, const float *kap, 
     opdf[i] = mixture_pdf<D, 8>(m, v);
 }
 
-wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *loss_out_dev);
+wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *loss_out_dev,
+                         long long off = -1);
+wost_status train_after_batch(wost_field *f, int dim, cudaStream_t st, int *steps);
 
 int guided_ctas_per_sm() { return 1; }
 
@@ -208,10 +210,11 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
     };
     auto train_after = [&]() -> wost_status {
         tm.mark(tm.train, st);
-        wost_status rc = train_launch(f, s->dim, st, true, nullptr);
+        int k = 0;
+        wost_status rc = train_after_batch(f, s->dim, st, &k);
         tm.mark(tm.train, st);
-        tm.launches += 5;   // gradient, Adam step count, Adam, FP16 grid copy, BF16 weight image
-        ntrain++;
+        tm.launches += 5 * k;   // per step: gradient, Adam step count, Adam, FP16 grid copy, BF16 weight image
+        ntrain += k;
         return rc;
     };
     g.rd = RecDest{f->rec, f->rec_ctr, f->rec_cap};

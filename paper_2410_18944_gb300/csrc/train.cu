@@ -47,6 +47,7 @@ struct TrainArgs {
     float *g_W1, *g_W2, *g_W3, *g_b3;
     double *loss_acc;
     long long max_samples;                  // records per step (0 = all)
+    long long off_fixed;                    // stratum of this step (< 0: from the Adam step count)
     const unsigned long long *step;         // Adam step count before this step
     unsigned long long *used;               // records this step used
     int *err;
@@ -188,7 +189,8 @@ __global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
     long long kstride = 1, off = 0, nrec = nall;
     if (a.max_samples > 0 && nall > a.max_samples) {
         kstride = (nall + a.max_samples - 1) / a.max_samples;
-        off = (long long)((*a.step * 2654435761ull) % (unsigned long long)kstride);
+        off = a.off_fixed >= 0 ? a.off_fixed % kstride
+                               : (long long)((*a.step * 2654435761ull) % (unsigned long long)kstride);
         nrec = (nall - off + kstride - 1) / kstride;
     }
     if (blockIdx.x == 0 && tid == 0) *a.used = (unsigned long long)nrec;
@@ -420,7 +422,7 @@ wost_status train_prepare(int dim) {
 }
 
 // gradient of the mean loss over the record buffer into f->grid_g / f->mlp_g
-wost_status train_grad_launch(wost_field *f, int dim, cudaStream_t st) {
+wost_status train_grad_launch(wost_field *f, int dim, cudaStream_t st, long long off) {
     WOST_CUDA(cudaMemsetAsync(f->grid_g, 0, f->n_grid() * sizeof(float), st));
     WOST_CUDA(cudaMemsetAsync(f->mlp_g, 0, f->n_mlp() * sizeof(float), st));
     WOST_CUDA(cudaMemsetAsync(f->loss_acc, 0, sizeof(double), st));
@@ -440,6 +442,7 @@ wost_status train_grad_launch(wost_field *f, int dim, cudaStream_t st) {
     a.g_b3 = a.g_W3 + (size_t)f->nout * kHid;
     a.loss_acc = reinterpret_cast<double *>(f->loss_acc);
     a.max_samples = f->t_samples;
+    a.off_fixed = off;
     a.step = f->adam_step();
     a.used = f->used_records();
     a.err = device_err_flag();
@@ -452,8 +455,8 @@ wost_status train_grad_launch(wost_field *f, int dim, cudaStream_t st) {
     return WOST_OK;
 }
 
-wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *) {
-    wost_status rc = train_grad_launch(f, dim, st);
+wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *, long long off) {
+    wost_status rc = train_grad_launch(f, dim, st, off);
     if (rc != WOST_OK || !apply_adam) return rc;
     const wost_field_desc &d = f->desc;
     int64_t ng = f->n_grid(), nm = f->n_mlp();
@@ -464,6 +467,29 @@ wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_ada
     adam_kernel<<<nba + nbb, 256, 0, st>>>(ga, gb, nba, d.beta1, d.beta2, d.adam_eps, f->adam_step());
     WOST_CUDA(cudaGetLastError());
     return refresh_inference_copy(f, st);
+}
+
+// Training after a batch of wost_solve (Sec. 5.2): one Adam step on every
+// record of the batch, or, with train_samples = m > 0, minibatches: the
+// batch's n records in k = ceil(n / m) strata of about m records (records
+// j, j + k, j + 2k, ...), one Adam step each, so every record is used once.
+wost_status train_after_batch(wost_field *f, int dim, cudaStream_t st, int *steps) {
+    *steps = 0;
+    if (f->t_samples <= 0) {
+        *steps = 1;
+        return train_launch(f, dim, st, true, nullptr, -1);
+    }
+    unsigned long long c = 0;
+    WOST_CUDA(cudaMemcpyAsync(&c, f->rec_ctr, sizeof(c), cudaMemcpyDeviceToHost, st));
+    WOST_CUDA(cudaStreamSynchronize(st));
+    const long long n = std::min<long long>((long long)c, (long long)f->rec_cap);
+    const long long k = n > f->t_samples ? (n + f->t_samples - 1) / f->t_samples : 1;
+    for (long long j = 0; j < k; ++j) {
+        wost_status rc = train_launch(f, dim, st, true, nullptr, k > 1 ? j : -1);
+        if (rc != WOST_OK) return rc;
+        ++*steps;
+    }
+    return WOST_OK;
 }
 
 }  // namespace wost

@@ -460,6 +460,27 @@ def test_train_step_on_a_strided_subset(api, dim):
     check(2654435761 % k)
 
 
+def test_online_training_in_minibatches(api):
+    # train_samples = m: after each batch of one walk per point the field
+    # takes ceil(n / m) Adam steps over the batch's n records; the estimate
+    # stays unbiased
+    sc = wi.half_disk(48, 12)
+    S = api.Scene(sc)
+    pts = _interior(sc, 64, 12)
+    F = api.Field(2, *sc.padded_bbox())
+    m, v, st = api.solve(S, pts, 2048, eps=1e-3, maxsteps=256, seed=21, guided=True, field=F, train=1,
+                         train_until_wpp=8, train_samples=256)
+    n_rec = st["records"]                # records of the last training batch
+    assert n_rec > 256 and st["train_steps"] >= 8 * 2
+    F2 = api.Field(2, *sc.padded_bbox())
+    m2, v2, st2 = api.solve(S, pts, 8, eps=1e-3, maxsteps=256, seed=21, guided=True, field=F2, train=1,
+                            train_until_wpp=8, train_samples=0)
+    assert st2["train_steps"] == 8
+    ex = wi.eval_fn(sc.exact, pts)
+    z = (m - ex) / np.sqrt(v)
+    assert np.all(np.isfinite(m)) and np.all(np.abs(z) < 4.5), z
+
+
 def test_online_training_runs_and_stays_unbiased(api):
     sc = wi.half_disk(48, 12)
     S = api.Scene(sc)
