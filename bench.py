@@ -408,14 +408,16 @@ def run_ours(args):
 WORKLOADS = {
     "sphere3d": dict(workload="3D mixed Dirichlet/Neumann Poisson guided WoSt: icosphere 81,920 triangles displaced "
                               "by 0.15 Perlin noise, 30% Neumann cap, f = 4 Gaussians (sigma 0.1), g = 1/|x - c|, "
-                              "256x256 slice z = 0 masked inside, 64 walks/point, online training after every batch, "
-                              "16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 MLP, K = 8",
-                     grid=256, spp=64, eps=1e-3, maxsteps=128, l2="flushed (512 MiB write) before each step"),
+                              "256x256 slice z = 0 masked inside, 64 walks/point, online training after every batch "
+                              "in minibatches of 2^18 records, 16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 "
+                              "MLP, K = 8",
+                     grid=256, spp=64, eps=1e-3, maxsteps=128, train_samples=1 << 18,
+                     l2="flushed (512 MiB write) before each step"),
     "genus3": dict(workload="3D mixed Dirichlet/Neumann Laplace guided WoSt with learned MIS selection: genus-3 "
                             "solid (sphere displaced by 0.15 Perlin noise minus three smoothly rimmed tunnels, "
                             "993,640 triangles by surface nets), 30% Neumann cap, g = 1/|x - c|, 1024x1024 slice "
-                            "z = 0 masked inside, 128 walks/point, online training after every batch on 2^18 "
-                            "records, 16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 MLP, K = 8",
+                            "z = 0 masked inside, 128 walks/point, online training after every batch in minibatches "
+                            "of 2^18 records, 16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 MLP, K = 8",
                    grid=1024, spp=128, eps=1e-3, maxsteps=128, train_samples=1 << 18,
                    l2="inputs larger than L2 (the BVHs and 1 M-walk batches); no flush"),
     "batch64": dict(workload="64 independent 2D star scenes (256-16384 segments log-uniform, Neumann fraction "
