@@ -180,6 +180,128 @@ __device__ __forceinline__ void query_leaf(LaneQuery<D> &Q, const DevScene &sc, 
     query_pop<D>(Q);
 }
 
+// Step values a lane carries between its queries.
+struct LaneStep {
+    float RD = 0.f;    // distance to the closest Dirichlet point
+    float r = 0.f;     // star radius
+    float rho = 0.f;   // source sample radius
+    float S = 0.f;     // source term of the step
+    int dslot = -1;    // closest Dirichlet leaf slot
+};
+
+enum : int {
+    kLaneGo = 0,      // the next query is set up
+    kLaneEnded = 1,   // the walk ended: value in w.acc, terminal value in gv
+    kLaneDirection = 2  // the step needs its direction (r and S are set)
+};
+
+// The step logic that follows a finished query (the walk-on-stars step of
+// walkstep.cuh, split at its queries):
+//   Dirichlet  -> epsilon-shell or step cap: end with T g(xbar); else the
+//                 silhouette query bounded by R_D;
+//   silhouette -> r = max(min(R_D, R_S), eps); the source-visibility ray, or
+//                 the direction;
+//   source ray -> source term -(r^2 / 2d) f(y) if visible; the direction;
+//   step ray   -> move (to the exit hit, tneg inside, or x + r nu); the next
+//                 step's Dirichlet query.
+template <int D>
+__device__ __forceinline__ int lane_after_query(Walk<D> &w, LaneQuery<D> &Q, LaneStep &L, const StepEnv &env,
+                                                float &gv, bool &trunc, unsigned long long &nsteps) {
+    const DevScene &sc = env.sc;
+    const float tneg = kRoundBand * sc.scale;
+    if (Q.q == kQDir) {
+        L.dslot = Q.slot;
+        L.RD = sqrtf(Q.best);
+        double q64[3];
+        bool have64 = false, shell;
+        if (fabsf(L.RD - env.eps) <= kRoundBand * (sc.scale + L.RD)) {
+            shell = dirichlet_dist64<D>(sc.dir, L.dslot, w.x, q64) <= env.eps64;
+            have64 = true;
+        } else {
+            shell = L.RD <= env.eps;
+        }
+        if (shell || w.k >= env.maxsteps) {
+            if (!have64) dirichlet_dist64<D>(sc.dir, L.dslot, w.x, q64);
+            float xb[3] = {(float)q64[0], (float)q64[1], D == 3 ? (float)q64[2] : 0.f};
+            gv = eval_fn<D>(sc.g, xb);
+            w.acc += w.T * gv;
+            trunc = !shell;
+            Q.q = kQNone;
+            return kLaneEnded;
+        }
+        query_begin<D>(Q, sc, kQSil, L.RD * L.RD);
+        return kLaneGo;
+    }
+    if (Q.q == kQSil) {
+        const float R = fminf(sqrtf(Q.best), L.RD);
+        L.r = fmaxf(R, env.eps);
+        L.S = 0.f;
+        if (!sc.has_source) return kLaneDirection;
+        U4 u = philox(w.pid, w.wid, (uint32_t)w.k, P_SRC, env.key0, env.key1);
+        float vs[D];
+        uniform_dir<D>(u01(u.x), u01(u.y), vs);
+        if (w.prim >= 0 && dotv<D>(vs, w.n) < 0.f) reflect<D>(vs, w.n);
+        L.rho = D == 2 ? L.r * sqrtf(u01(u.z) * u01(u.w)) : L.r * beta22_inv(u01(u.z));
+        query_ray<D>(Q, sc, kQSrc, vs, L.rho);
+        return kLaneGo;
+    }
+    if (Q.q == kQSrc) {
+        int hs = Q.slot;
+        const float th = Q.best;
+        if (hs >= 0 && L.rho - th <= kRoundBand * (sc.scale + L.rho)) {
+            double t64;
+            if (!ray_prim64<D, true>(sc.neu, hs, w.x, Q.v, t64, tneg) || t64 > (double)L.rho) hs = -1;
+        }
+        L.S = 0.f;
+        if (hs < 0) {
+            float y[3];
+#pragma unroll
+            for (int i = 0; i < D; ++i) y[i] = w.x[i] + L.rho * Q.v[i];
+            L.S = -(L.r * L.r / (2.f * D)) * eval_fn<D>(sc.f, y);
+        }
+        w.acc += w.T * L.S;
+        return kLaneDirection;
+    }
+    // kQMove
+    int hit = Q.slot;
+    float th = Q.best;
+    if (hit >= 0 && L.r - th <= kRoundBand * (sc.scale + L.r)) {
+        double t64;
+        if (!ray_prim64<D, true>(sc.neu, hit, w.x, Q.v, t64, tneg) || t64 > (double)L.r) hit = -1;
+    }
+    if (hit >= 0) {
+        // exit hit: stand tneg inside along the primitive's inward normal
+        th = fmaxf(th, 0.f);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            w.n[i] = __ldg(sc.nin_neu + (size_t)hit * D + i);
+            w.x[i] += th * Q.v[i] + tneg * w.n[i];
+        }
+        w.prim = hit;
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) w.x[i] += L.r * Q.v[i];
+        w.prim = -1;
+    }
+    w.k++;
+    nsteps++;
+    query_begin<D>(Q, sc, kQDir, __int_as_float(0x7f800000));
+    return kLaneGo;
+}
+
+// One node or leaf phase of the lanes that are searching (all lanes of the
+// warp take part).
+template <int D, class Src>
+__device__ __forceinline__ void lanes_traverse(const Src &src, const Walk<D> &w, LaneQuery<D> &Q, bool searching,
+                                               Visits &vis) {
+    const StepEnv env = src.env(w);
+    const float tneg = kRoundBand * env.sc.scale;
+    while (__any_sync(0xffffffffu, searching && !Q.fin && Q.ref >= 0)) {
+        if (searching && !Q.fin && Q.ref >= 0) query_node<D>(Q, env.sc, w.x, tneg, env.err, vis);
+    }
+    if (searching && !Q.fin) query_leaf<D>(Q, env.sc, w.x, w.prim, tneg, vis);
+}
+
 // The plain walk (uniform directions, reflection at Neumann points) over a
 // job source, step for step the computation of plain_loop: the same random
 // numbers, tests and updates in the same order per walk.
@@ -189,97 +311,22 @@ __device__ __forceinline__ void plain_loop_lanes(const Src &src, unsigned long l
     w.job = 0;        // a lane without a walk still names a valid job
     w.prim = -1;
     LaneQuery<D> Q;
+    LaneStep L;
     Visits vis;
     bool active = false, exhausted = false;
     unsigned long long nsteps = 0, ntrunc = 0, nwalks = 0;
-    float RD = 0.f, r = 0.f, rho = 0.f;
-    int dslot = -1;
-    const float kInf = __int_as_float(0x7f800000);
     for (;;) {
         // ---- logic phase ----
         if (Q.fin && Q.q != kQNone) {
             const StepEnv env = src.env(w);
-            const DevScene &sc = env.sc;
-            const float tneg = kRoundBand * sc.scale;
-            bool dir_move = false;   // draw the step direction and cast the step ray
-            if (Q.q == kQDir) {
-                float bd2 = Q.best;
-                dslot = Q.slot;
-                RD = sqrtf(bd2);
-                double q64[3];
-                bool have64 = false, shell;
-                if (fabsf(RD - env.eps) <= kRoundBand * (sc.scale + RD)) {
-                    shell = dirichlet_dist64<D>(sc.dir, dslot, w.x, q64) <= env.eps64;
-                    have64 = true;
-                } else {
-                    shell = RD <= env.eps;
-                }
-                if (shell || w.k >= env.maxsteps) {
-                    if (!have64) dirichlet_dist64<D>(sc.dir, dslot, w.x, q64);
-                    float xb[3] = {(float)q64[0], (float)q64[1], D == 3 ? (float)q64[2] : 0.f};
-                    w.acc += w.T * eval_fn<D>(sc.g, xb);
-                    src.finish(w);
-                    ntrunc += !shell;
-                    active = false;
-                    Q.q = kQNone;
-                } else {
-                    query_begin<D>(Q, sc, kQSil, RD * RD);
-                }
-            } else if (Q.q == kQSil) {
-                float R = fminf(sqrtf(Q.best), RD);
-                r = fmaxf(R, env.eps);
-                if (sc.has_source) {
-                    U4 u = philox(w.pid, w.wid, (uint32_t)w.k, P_SRC, env.key0, env.key1);
-                    float vs[D];
-                    uniform_dir<D>(u01(u.x), u01(u.y), vs);
-                    if (w.prim >= 0 && dotv<D>(vs, w.n) < 0.f) reflect<D>(vs, w.n);
-                    rho = D == 2 ? r * sqrtf(u01(u.z) * u01(u.w)) : r * beta22_inv(u01(u.z));
-                    query_ray<D>(Q, sc, kQSrc, vs, rho);
-                } else {
-                    dir_move = true;
-                }
-            } else if (Q.q == kQSrc) {
-                int hs = Q.slot;
-                const float th = Q.best;
-                if (hs >= 0 && rho - th <= kRoundBand * (sc.scale + rho)) {
-                    double t64;
-                    if (!ray_prim64<D, true>(sc.neu, hs, w.x, Q.v, t64, tneg) || t64 > (double)rho) hs = -1;
-                }
-                float S = 0.f;
-                if (hs < 0) {
-                    float y[3];
-#pragma unroll
-                    for (int i = 0; i < D; ++i) y[i] = w.x[i] + rho * Q.v[i];
-                    S = -(r * r / (2.f * D)) * eval_fn<D>(sc.f, y);
-                }
-                w.acc += w.T * S;
-                dir_move = true;
-            } else if (Q.q == kQMove) {
-                int hit = Q.slot;
-                float th = Q.best;
-                if (hit >= 0 && r - th <= kRoundBand * (sc.scale + r)) {
-                    double t64;
-                    if (!ray_prim64<D, true>(sc.neu, hit, w.x, Q.v, t64, tneg) || t64 > (double)r) hit = -1;
-                }
-                if (hit >= 0) {
-                    // exit hit: stand tneg inside along the primitive's inward normal
-                    th = fmaxf(th, 0.f);
-#pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        w.n[i] = __ldg(sc.nin_neu + (size_t)hit * D + i);
-                        w.x[i] += th * Q.v[i] + tneg * w.n[i];
-                    }
-                    w.prim = hit;
-                } else {
-#pragma unroll
-                    for (int i = 0; i < D; ++i) w.x[i] += r * Q.v[i];
-                    w.prim = -1;
-                }
-                w.k++;
-                nsteps++;
-                query_begin<D>(Q, sc, kQDir, kInf);
-            }
-            if (dir_move) {
+            float gv = 0.f;
+            bool trunc = false;
+            const int res = lane_after_query<D>(w, Q, L, env, gv, trunc, nsteps);
+            if (res == kLaneEnded) {
+                src.finish(w);
+                ntrunc += trunc;
+                active = false;
+            } else if (res == kLaneDirection) {
                 U4 u = philox(w.pid, w.wid, (uint32_t)w.k, P_DIR, env.key0, env.key1);
                 float nu[D];
                 uniform_dir<D>(u01(u.x), u01(u.y), nu);
@@ -294,7 +341,7 @@ __device__ __forceinline__ void plain_loop_lanes(const Src &src, unsigned long l
                     active = false;
                     Q.q = kQNone;
                 } else {
-                    query_ray<D>(Q, sc, kQMove, nu, r);
+                    query_ray<D>(Q, env.sc, kQMove, nu, L.r);
                 }
             }
         }
@@ -306,7 +353,7 @@ __device__ __forceinline__ void plain_loop_lanes(const Src &src, unsigned long l
                 active = true;
                 nwalks++;
                 nsteps++;
-                query_begin<D>(Q, src.env(w).sc, kQDir, kInf);
+                query_begin<D>(Q, src.env(w).sc, kQDir, __int_as_float(0x7f800000));
             }
         }
         if (!__any_sync(0xffffffffu, active || !exhausted)) break;
@@ -314,12 +361,7 @@ __device__ __forceinline__ void plain_loop_lanes(const Src &src, unsigned long l
         const bool searching = active && !Q.fin;
         if (!__any_sync(0xffffffffu, searching)) continue;
         // ---- node and leaf phases ----
-        const StepEnv env = src.env(w);
-        const float tneg = kRoundBand * env.sc.scale;
-        while (__any_sync(0xffffffffu, searching && !Q.fin && Q.ref >= 0)) {
-            if (searching && !Q.fin && Q.ref >= 0) query_node<D>(Q, env.sc, w.x, tneg, env.err, vis);
-        }
-        if (searching && !Q.fin) query_leaf<D>(Q, env.sc, w.x, w.prim, tneg, vis);
+        lanes_traverse<D>(src, w, Q, searching, vis);
     }
     flush_stats(stat, nsteps, ntrunc, nwalks, vis);
 }
