@@ -588,9 +588,11 @@ def run_once(args):
     F = api.Field(dim, lo, hi)
     p = torch.tensor(pts, dtype=torch.float64, device="cuda")
     guided = args.once == "guided"
+    ts = WORKLOADS.get(args.workload, {}).get("train_samples", 0)
     for rep in range(2):
         m, v, st = api.solve(S, p, args.spp, eps=WORKLOAD["eps"], maxsteps=WORKLOAD["maxsteps"], seed=rep,
-                             guided=guided, field=F if guided else None, train=1 if guided else 0)
+                             guided=guided, field=F if guided else None, train=1 if guided else 0,
+                             train_samples=ts if guided else 0)
         torch.cuda.synchronize()
         print(json.dumps({"once": args.once, "rep": rep, **{k: st[k] for k in (
             "walk_steps", "ms_walk", "ms_train", "node_visits", "prim_visits", "kernel_launches", "records")}}))
