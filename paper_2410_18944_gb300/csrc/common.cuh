@@ -109,7 +109,7 @@ struct DevScene {
     float scale;          // bounding-box diagonal
     float tau;            // silhouette edge-on tolerance (1e-6 * scale)
     DevBVH dir, neu, sil;
-    const float4 *sil_cones;  // per silhouette-BVH node: normal cones of child 0 and 1 (axis.xyz, cos half-angle)
+    const float4 *sil_cones;  // per silhouette-BVH node: one normal cone per child (axis.xyz, cos half-angle)
     const float *nin_neu; // inward normal of each Neumann prim, by original id (dim floats)
     DevFn g, f;
     int has_source;

@@ -75,13 +75,13 @@ struct SoloSrc {
 constexpr int kStageRegions = 7;
 
 __host__ __device__ __forceinline__ void stage_regions(const DevScene &s, const float4 **src, int *cnt) {
-    const int nb = s.dim == 2 ? 3 : 4;       // float4 per node
+    const int nb = s.dim == 2 ? node_f4<2>() : node_f4<3>();   // float4 per node
     const int pd = s.dim == 2 ? 1 : 3;       // per Dirichlet / Neumann primitive
     const int ps = s.dim == 2 ? 2 : 4;       // per silhouette element
     src[0] = s.dir.nodes; cnt[0] = s.dir.nnodes * nb;
     src[1] = s.neu.nodes; cnt[1] = s.neu.nnodes * nb;
     src[2] = s.sil.nodes; cnt[2] = s.sil.nnodes * nb;
-    src[3] = s.sil_cones; cnt[3] = s.sil_cones ? 2 * s.sil.nnodes : 0;
+    src[3] = s.sil_cones; cnt[3] = s.sil_cones ? bvh_width(s.dim) * s.sil.nnodes : 0;
     src[4] = s.dir.prims; cnt[4] = s.dir.nprims * pd;
     src[5] = s.neu.prims; cnt[5] = s.neu.nprims * pd;
     src[6] = s.sil.prims; cnt[6] = s.sil.nprims * ps;

@@ -82,36 +82,24 @@ __device__ __forceinline__ void query_pop(LaneQuery<D> &Q) {
 template <int D>
 __device__ __forceinline__ void query_node(LaneQuery<D> &Q, const DevScene &sc, const float *x, float tneg,
                                            int *err, Visits &vis) {
+    constexpr int kBW = bvh_width(D);
     const DevBVH &bv = query_bvh<D>(sc, Q.q);
-    float k0, k1;
-    int r0, r1;
-    if (Q.q == kQDir || Q.q == kQSil) node_box_d2<D>(bv.nodes, Q.ref, x, k0, k1, r0, r1);
-    else node_box_ray<D>(bv.nodes, Q.ref, x, Q.inv, Q.best, k0, k1, r0, r1, tneg);
+    float k[kBW];
+    int r[kBW];
+    bool h[kBW];
+    if (Q.q == kQDir || Q.q == kQSil) node_keys_d2<D>(bv.nodes, Q.ref, x, k, r);
+    else node_keys_ray<D>(bv.nodes, Q.ref, x, Q.inv, Q.best, k, r, tneg);
     vis.nodes++;
-    bool h0 = k0 <= Q.best, h1 = k1 <= Q.best;
-    if (Q.q == kQSil && sc.sil_cones && (h0 || h1)) {
-        float lo0[3], hi0[3], lo1[3], hi1[3];
-        child_boxes<D>(bv.nodes, Q.ref, lo0, hi0, lo1, hi1);
-        if (h0 && cone_prunes<D>(ldn(sc.sil_cones + 2 * Q.ref), lo0, hi0, x, k0, sc.tau)) h0 = false;
-        if (h1 && cone_prunes<D>(ldn(sc.sil_cones + 2 * Q.ref + 1), lo1, hi1, x, k1, sc.tau)) h1 = false;
-    }
-    if (h0 && h1) {
-        const bool first0 = k0 <= k1;
-        if (Q.sp < kStack) {
-            Q.stack[Q.sp] = first0 ? r1 : r0;
-            Q.key[Q.sp] = first0 ? k1 : k0;
-            ++Q.sp;
-        } else {
-            atomicOr(err, 1);
+#pragma unroll
+    for (int c = 0; c < kBW; ++c) {
+        h[c] = r[c] != kEmptyRef && k[c] <= Q.best;
+        if (Q.q == kQSil && sc.sil_cones && h[c]) {
+            float lo[3], hi[3];
+            node_child_box<D>(bv.nodes, Q.ref, c, lo, hi);
+            if (cone_prunes<D>(ldn(sc.sil_cones + kBW * Q.ref + c), lo, hi, x, k[c], sc.tau)) h[c] = false;
         }
-        Q.ref = first0 ? r0 : r1;
-    } else if (h0) {
-        Q.ref = r0;
-    } else if (h1) {
-        Q.ref = r1;
-    } else {
-        query_pop<D>(Q);
     }
+    if (!take_children<kBW>(k, r, h, Q.ref, Q.stack, Q.key, Q.sp, err)) query_pop<D>(Q);
 }
 
 // one leaf: test its primitives, then continue from the stack

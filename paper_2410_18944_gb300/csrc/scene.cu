@@ -9,6 +9,7 @@
 #include <cstring>
 #include <numeric>
 
+#include "geom.cuh"
 #include "internal.h"
 
 namespace wost {
@@ -180,23 +181,106 @@ struct Builder {
         return maxdepth < 62;   // device traversal stack holds 64 entries
     }
 
-    // two cones per node (children 0 and 1)
+    // ---- device layout ----
+    // Width 2: the binary nodes, child boxes in the parent.  Width 4: each
+    // node takes up to four descendants of a binary node (its children, with
+    // the inner child of the larger box surface opened until there are
+    // four); empty slots carry kEmptyRef and an inverted box.
+    struct Child { Box box; int ref; int range[2]; };
+    struct WNode { Child ch[4]; int n; };
+    std::vector<WNode> wide;
+    int wdepth = 0;
+
+    int collapse(int bnode, int depth) {
+        wdepth = std::max(wdepth, depth);
+        Child ch[4];
+        int n = 0;
+        for (int c = 0; c < 2; ++c)
+            ch[n++] = Child{nodes[bnode].box[c], nodes[bnode].ref[c], {nodes[bnode].range[c][0], nodes[bnode].range[c][1]}};
+        while (n < 4) {
+            int pick = -1;
+            float area = -1.f;
+            for (int i = 0; i < n; ++i)
+                if (ch[i].ref >= 0 && ch[i].box.cost(d) > area) { pick = i; area = ch[i].box.cost(d); }
+            if (pick < 0) break;
+            const BNode &b = nodes[ch[pick].ref];
+            Child c0{b.box[0], b.ref[0], {b.range[0][0], b.range[0][1]}};
+            Child c1{b.box[1], b.ref[1], {b.range[1][0], b.range[1][1]}};
+            ch[pick] = c0;
+            ch[n++] = c1;
+        }
+        const int id = (int)wide.size();
+        wide.push_back(WNode{});
+        for (int i = 0; i < 4; ++i) {
+            Child c;
+            if (i < n) {
+                c = ch[i];
+                if (c.ref >= 0) c.ref = collapse(c.ref, depth + 1);
+            } else {
+                c = Child{Box{}, kEmptyRef, {0, 0}};
+            }
+            wide[id].ch[i] = c;
+        }
+        wide[id].n = n;
+        return id;
+    }
+
+    // most stack entries a traversal below wide node id can hold: a visit
+    // pushes all but one of its taken children
+    int stack_need(int id) const {
+        int need = 0;
+        for (int c = 0; c < 4; ++c)
+            if (wide[id].ch[c].ref >= 0) need = std::max(need, stack_need(wide[id].ch[c].ref));
+        return need + std::max(wide[id].n - 1, 0);
+    }
+
+    // builds the wide tree (width 4); false if a traversal could overflow
+    // the device stack
+    bool widen() {
+        wide.clear();
+        wdepth = 0;
+        if (bvh_width(d) == 2 || nodes.empty()) return true;
+        collapse(0, 1);
+        return stack_need(0) < kStack;
+    }
+
+    int device_nodes() const { return bvh_width(d) == 2 ? (int)nodes.size() : (int)wide.size(); }
+
+    // one cone per child
     std::vector<float4> cones() const {
         std::vector<float4> out;
-        for (const BNode &nd : nodes)
-            for (int c = 0; c < 2; ++c)
-                out.push_back(nd.range[c][1] > nd.range[c][0] ? normal_cone(items, nd.range[c][0], nd.range[c][1], d)
-                                                                : make_float4(0.f, 0.f, 0.f, -2.f));
+        auto cone = [&](int b, int e) {
+            return e > b ? normal_cone(items, b, e, d) : make_float4(0.f, 0.f, 0.f, -2.f);
+        };
+        if (bvh_width(d) == 2) {
+            for (const BNode &nd : nodes)
+                for (int c = 0; c < 2; ++c) out.push_back(cone(nd.range[c][0], nd.range[c][1]));
+        } else {
+            for (const WNode &wn : wide)
+                for (int c = 0; c < 4; ++c) out.push_back(cone(wn.ch[c].range[0], wn.ch[c].range[1]));
+        }
         return out;
     }
 
     std::vector<float4> pack() const {
         std::vector<float4> out;
+        auto bits = [](int r) { float f; std::memcpy(&f, &r, 4); return f; };
+        if (bvh_width(d) == 4) {
+            // one coordinate of the four children per float4: lo x, lo y, (lo z,) hi x, hi y, (hi z,) refs
+            for (const WNode &wn : wide) {
+                for (int side = 0; side < 2; ++side)
+                    for (int a = 0; a < d; ++a) {
+                        float v[4];
+                        for (int c = 0; c < 4; ++c) v[c] = side == 0 ? wn.ch[c].box.lo[a] : wn.ch[c].box.hi[a];
+                        out.push_back(make_float4(v[0], v[1], v[2], v[3]));
+                    }
+                out.push_back(make_float4(bits(wn.ch[0].ref), bits(wn.ch[1].ref), bits(wn.ch[2].ref), bits(wn.ch[3].ref)));
+            }
+            return out;
+        }
         for (const BNode &nd : nodes) {
             const Box &a = nd.box[0], &b = nd.box[1];
-            float r0, r1;
-            std::memcpy(&r0, &nd.ref[0], 4);
-            std::memcpy(&r1, &nd.ref[1], 4);
+            float r0 = bits(nd.ref[0]), r1 = bits(nd.ref[1]);
             if (d == 2) {
                 out.push_back(make_float4(a.lo[0], a.lo[1], a.hi[0], a.hi[1]));
                 out.push_back(make_float4(b.lo[0], b.lo[1], b.hi[0], b.hi[1]));
@@ -338,7 +422,7 @@ extern "C" wost_status wost_create_scene(const wost_scene_desc *desc, wost_scene
             B.items.push_back(it);
         }
         count = (int)B.items.size();
-        if (!B.build()) { set_error("wost_create_scene: BVH too deep"); return WOST_ERR_INVALID_ARG; }
+        if (!B.build() || !B.widen()) { set_error("wost_create_scene: BVH too deep"); return WOST_ERR_INVALID_ARG; }
         depth = B.maxdepth;
         std::vector<float4> prims;
         std::vector<double> p64;
@@ -361,7 +445,7 @@ extern "C" wost_status wost_create_scene(const wost_scene_desc *desc, wost_scene
         }
         wost_status st;
         if ((st = upload(s, B.pack(), &bv.nodes)) != WOST_OK) return st;
-        bv.nnodes = (int)B.nodes.size();
+        bv.nnodes = B.device_nodes();
         if ((st = upload(s, prims, &bv.prims)) != WOST_OK) return st;
         if ((st = upload(s, ids, &bv.ids)) != WOST_OK) return st;
         if ((st = upload(s, p64, &bv.prims64)) != WOST_OK) return st;
@@ -432,7 +516,7 @@ extern "C" wost_status wost_create_scene(const wost_scene_desc *desc, wost_scene
             B.items.push_back(it);
         }
         s->nsil = (int)el.size();
-        if (!B.build()) { set_error("wost_create_scene: BVH too deep"); delete s; return WOST_ERR_INVALID_ARG; }
+        if (!B.build() || !B.widen()) { set_error("wost_create_scene: BVH too deep"); delete s; return WOST_ERR_INVALID_ARG; }
         s->depth_sil = B.maxdepth;
         std::vector<float4> prims;
         std::vector<int> ids;
@@ -464,7 +548,7 @@ extern "C" wost_status wost_create_scene(const wost_scene_desc *desc, wost_scene
             delete s;
             return st;
         }
-        bv.nnodes = (int)B.nodes.size();
+        bv.nnodes = B.device_nodes();
         const int64_t *kp = nullptr;
         if ((st = upload(s, keys, &kp)) != WOST_OK) { delete s; return st; }
         s->sil_key = const_cast<int64_t *>(kp);

@@ -21,7 +21,8 @@ namespace wost {
 
 double walk_alg_bytes(int D, bool guided, const unsigned long long *hs, int64_t records) {
     // bytes per item of the leaf-order arrays (see common.cuh)
-    const double node_b = D == 2 ? 48 : 64, prim_b = D == 2 ? 16 : 48, sil_b = D == 2 ? 32 : 64;
+    const double node_b = 16.0 * (D == 2 ? node_f4<2>() : node_f4<3>()), prim_b = D == 2 ? 16 : 48,
+                 sil_b = D == 2 ? 32 : 64;
     double b = hs[3] * node_b + hs[4] * prim_b + hs[5] * sil_b + hs[6] * prim_b;
     b += (double)hs[2] * (D * 8.0 + 2 * 8.0);          // start point, FP64 sum and sum of squares
     if (guided) {
