@@ -53,11 +53,16 @@ constexpr int kWsServerWarps = 4;
 #define WOST_WS_WALKERS 12
 #endif
 #ifndef WOST_WS_TILES
-#define WOST_WS_TILES 2
+#define WOST_WS_TILES 1
 #endif
 constexpr int kWsWalkerWarps = WOST_WS_WALKERS;
 constexpr int kWsThreads = 32 * (kWsServerWarps + kWsWalkerWarps);
-constexpr int kNT = WOST_WS_TILES;           // decode tile buffers (few: leaves L1 for the BVH)
+// decode tile buffers.  Measured on one GB300: one buffer is 6% faster than
+// two on the 2D star and 3-5% on the icosphere (equal on the genus-3 solid);
+// three and four are slower still.  A walker warp that finds the buffer busy
+// waits for the tile in flight, so tiles fill fuller and the shared memory
+// the buffers do not take goes to the scene and to L1.
+constexpr int kNT = WOST_WS_TILES;
 constexpr uint32_t kWsTmemCols = tmem_cols(kNT * 64);   // allocation rounded up to a power of two
 static_assert(kNT >= 1 && kNT * 64 <= 512, "decode tile buffers must fit in the 512 TMEM columns");
 // The `full` and `done` barriers of a buffer can never run two phases ahead
