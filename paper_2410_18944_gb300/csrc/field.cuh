@@ -89,12 +89,20 @@ __device__ __forceinline__ void unit_coords(const DevField &f, const float *x, f
 }
 
 // encode one position into a row of the bf16 feature tile (kFeat columns)
+// groups of four levels whose corner gathers are in flight together (two
+// groups measured 3-4% slower in the warp-specialised walk kernel and no
+// faster in training, at 14-18 more registers)
+#ifndef WOST_ENCODE_UNROLL
+#define WOST_ENCODE_UNROLL 1
+#endif
+constexpr int kEncodeUnroll = WOST_ENCODE_UNROLL;
+
 template <int D>
 __device__ __forceinline__ void encode_row(const DevField &f, const float *x, uint8_t *xtile, int row) {
     float u[D];
     unit_coords<D>(f, x, u);
     const size_t T = (size_t)1 << f.log2T;
-#pragma unroll 1
+#pragma unroll kEncodeUnroll
     for (int l4 = 0; l4 < kMaxLevels; l4 += 4) {
         float feat[8];
 #pragma unroll
