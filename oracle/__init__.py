@@ -58,14 +58,15 @@ _u32p = C.POINTER(C.c_uint32)
 class Params(C.Structure):
     _fields_ = [("eps", C.c_double), ("maxsteps", C.c_int), ("guided", C.c_int),
                 ("c_mode", C.c_int), ("c_fixed", C.c_double), ("reflect", C.c_int),
-                ("seed", C.c_uint64), ("scene_id", C.c_uint32), ("nthreads", C.c_int)]
+                ("seed", C.c_uint64), ("scene_id", C.c_uint32), ("nthreads", C.c_int),
+                ("rr_depth", C.c_int), ("rr_survival", C.c_double)]
 
 
 class _Field(C.Structure):
     _fields_ = [("dim", C.c_int), ("K", C.c_int), ("L", C.c_int), ("log2T", C.c_int),
                 ("F", C.c_int), ("H", C.c_int), ("base_res", C.c_int), ("max_res", C.c_int),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3),
-                ("grid", _dp), ("W1", _dp), ("W2", _dp), ("W3", _dp), ("b3", _dp)]
+                ("grid", _dp), ("W1", _dp), ("W2", _dp), ("W3", _dp), ("b3", _dp), ("grid_type", C.c_int)]
 
 
 def _declare(L):
@@ -74,7 +75,9 @@ def _declare(L):
     L.orc_u01.argtypes = [C.c_uint32]
     L.orc_scene_create.restype = C.c_void_p
     L.orc_scene_create.argtypes = [C.c_int, C.c_int, _dp, C.c_int, _ip, C.POINTER(C.c_uint8),
-                                   C.c_int, _dp, C.c_int, C.c_int, _dp, C.c_int]
+                                   C.c_int, _dp, C.c_int, C.c_int, _dp, C.c_int, C.c_int, _dp, C.c_int]
+    L.orc_neumann_sample.argtypes = [C.c_void_p, _dp, C.c_double, _u32p, C.c_uint32, C.c_uint32, C.c_uint32,
+                                     _dp, _dp]
     L.orc_scene_free.argtypes = [C.c_void_p]
     L.orc_scene_nsil.argtypes = [C.c_void_p]
     L.orc_scene_scale.argtypes = [C.c_void_p]
@@ -104,6 +107,8 @@ def _declare(L):
     L.orc_mixture_pdf.restype = C.c_double
     L.orc_mixture_pdf.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp]
     L.orc_field_nout.argtypes = [C.POINTER(_Field)]
+    L.orc_field_entries.restype = C.c_int64
+    L.orc_field_entries.argtypes = [C.POINTER(_Field)]
     L.orc_level_res.argtypes = [C.POINTER(_Field), C.c_int]
     L.orc_field_encode.argtypes = [C.POINTER(_Field), _dp, _dp]
     L.orc_field_forward.argtypes = [C.POINTER(_Field), _dp, _dp]
@@ -112,6 +117,9 @@ def _declare(L):
     L.orc_walk.restype = C.c_double
     L.orc_walk.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(Params), C.c_uint32, C.c_uint32, _dp,
                            _ip, _ip, _dp, C.c_int, _ip]
+    L.orc_walk_terms.restype = C.c_double
+    L.orc_walk_terms.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(Params), C.c_uint32, C.c_uint32, _dp,
+                                 _ip, _ip, _dp, C.c_int, _ip, _dp]
     L.orc_solve.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(Params), _dp, C.c_int, C.c_int, C.c_int,
                             _dp, _dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _dp, _ip]
     L.orc_train_loss.restype = C.c_double
@@ -154,11 +162,12 @@ class Scene:
         V = _f64(sc.verts)
         P = np.ascontiguousarray(sc.prims, np.int32)
         bc = np.ascontiguousarray(sc.bc, np.uint8)
-        g = _f64(list(sc.g.params) + [0.0] * 4)
-        f = _f64(list(sc.f.params) + [0.0] * 4)
+        g = _f64(list(sc.g.params) + [0.0] * 10)
+        f = _f64(list(sc.f.params) + [0.0] * 10)
+        h = _f64(list(sc.h.params) + [0.0] * 10)
         self._h = lib().orc_scene_create(sc.dim, len(V), _d(V), len(P), P.ctypes.data_as(_ip),
                                          bc.ctypes.data_as(C.POINTER(C.c_uint8)), sc.g.kind, _d(g),
-                                         len(g), sc.f.kind, _d(f), len(f))
+                                         len(g), sc.f.kind, _d(f), len(f), sc.h.kind, _d(h), len(h))
 
     def __del__(self):
         if getattr(self, "_h", None) and lib is not None:
@@ -216,6 +225,16 @@ class Scene:
             idx[i] = fn(self._h, _d(org[i]), _d(dirs[i]), float(tmax[i]), int(skip[i]), C.byref(tt))
             t[i] = tt.value
         return idx, t
+
+    def neumann_sample(self, x, r, key, pid, wid, step):
+        """(primitive, z, W) of the <N> sample at x within radius r."""
+        x3 = np.zeros(3)
+        x3[:self.dim] = x
+        z = np.zeros(3)
+        W = C.c_double()
+        k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+        i = lib().orc_neumann_sample(self._h, _d(x3), float(r), k, pid, wid, step, _d(z), C.byref(W))
+        return i, z[:self.dim], W.value
 
     def winding(self, pts):
         pts = _f64(pts)
@@ -304,6 +323,7 @@ class FieldParams:
     W2: np.ndarray
     W3: np.ndarray
     b3: np.ndarray
+    grid_type: int = 0       # 0 hash grid, 1 dense grid
 
     @property
     def nout(self):
@@ -321,7 +341,9 @@ class Field:
         hi = list(fp.hi) + [1.0] * (3 - len(fp.hi))
         self.s = _Field(fp.dim, fp.K, fp.L, fp.log2T, fp.F, fp.H, fp.base_res, fp.max_res,
                         (C.c_double * 3)(*lo), (C.c_double * 3)(*hi),
-                        *[_d(a) for a in self._arrs])
+                        *[_d(a) for a in self._arrs], int(fp.grid_type))
+        if self._arrs[0].size != lib().orc_field_entries(self.ref()) * fp.F:
+            raise ValueError("grid size does not match the encoding")
 
     def ref(self):
         return C.byref(self.s)
@@ -381,22 +403,31 @@ def adam(p, g, m, v, lr, b1, b2, eps, t):
 # ---- walks ------------------------------------------------------------------
 
 def make_params(eps=1e-3, maxsteps=128, guided=0, c_mode=0, c_fixed=0.5, reflect=1, seed=1,
-                scene_id=0, nthreads=None):
+                scene_id=0, nthreads=None, rr_depth=0, rr_survival=0.95):
     return Params(eps, maxsteps, guided, c_mode, c_fixed, reflect, seed, scene_id,
-                  nthreads or os.cpu_count() or 1)
+                  nthreads or os.cpu_count() or 1, rr_depth, rr_survival)
 
 
 def walk(scene: Scene, prm: Params, pid, wid, x0, field: Optional[Field] = None, records=False):
+    """One walk.  With ``records``: its training records, and ``w`` / ``S``
+    (each record's step weight and source term) and ``last`` (the walk's
+    final value), the inputs of the suffix pass."""
     x = np.zeros(3)
     x[:scene.dim] = x0
     st, tr, nr = C.c_int32(), C.c_int32(), C.c_int32()
     recs = np.zeros((prm.maxsteps, REC)) if records else None
-    v = lib().orc_walk(scene._h, C.cast(C.byref(field.s), C.c_void_p) if field else None, C.byref(prm),
-                       pid, wid, _d(x), C.byref(st), C.byref(tr),
-                       _d(recs) if records else C.cast(None, _dp), prm.maxsteps, C.byref(nr))
+    terms = np.zeros(2 * prm.maxsteps + 1) if records else None
+    v = lib().orc_walk_terms(scene._h, C.cast(C.byref(field.s), C.c_void_p) if field else None, C.byref(prm),
+                             pid, wid, _d(x), C.byref(st), C.byref(tr),
+                             _d(recs) if records else C.cast(None, _dp), prm.maxsteps, C.byref(nr),
+                             _d(terms) if records else C.cast(None, _dp))
     out = dict(value=v, steps=st.value, truncated=tr.value)
     if records:
-        out["records"] = recs[:nr.value].copy()
+        n = nr.value
+        out["records"] = recs[:n].copy()
+        out["w"] = terms[0:2 * n:2].copy()
+        out["S"] = terms[1:2 * n:2].copy()
+        out["last"] = float(terms[2 * n])
     return out
 
 

@@ -12,6 +12,10 @@
  * T = 2^log2T is indexed densely (x fastest), finer levels by the spatial
  * hash (i * 1) xor (j * 2654435761) xor (k * 805459861) mod T.
  * Positions are mapped to [0,1]^d by the box [lo, hi].
+ *
+ * Dense grid (grid_type 1; the encoding the paper uses, Sec. 5.2): the same
+ * levels, every one stored densely with its own (N_l + 1)^d vertices, level l
+ * starting at entry sum_{j<l} (N_j + 1)^d.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -28,12 +32,30 @@ int orc_level_res(const orc_field *f, int l)
     return (int)floor(f->base_res * pow(b, l) + 1e-6);
 }
 
+static int64_t level_vertices(const orc_field *f, int l)
+{
+    int64_t side = orc_level_res(f, l) + 1, n = 1;
+    for (int k = 0; k < f->dim; ++k) n *= side;
+    return n;
+}
+
+/* first entry of level l in the grid array */
+static int64_t level_offset(const orc_field *f, int l)
+{
+    if (f->grid_type == 0) return (int64_t)l << f->log2T;
+    int64_t off = 0;
+    for (int j = 0; j < l; ++j) off += level_vertices(f, j);
+    return off;
+}
+
+int64_t orc_field_entries(const orc_field *f) { return level_offset(f, f->L); }
+
 /* corner c (bit k of c selects +1 along axis k) of the cell around x:
-   lattice index and interpolation weight */
+   grid-array entry (level offset included) and interpolation weight */
 static void level_corners(const orc_field *f, int l, const double *x, int64_t *idx, double *w)
 {
     int d = f->dim, N = orc_level_res(f, l);
-    int64_t T = (int64_t)1 << f->log2T;
+    int64_t T = (int64_t)1 << f->log2T, off = level_offset(f, l);
     int64_t cell[3];
     double fr[3];
     for (int k = 0; k < d; ++k) {
@@ -56,7 +78,7 @@ static void level_corners(const orc_field *f, int l, const double *x, int64_t *i
             wt *= bit ? fr[k] : 1 - fr[k];
         }
         int64_t id;
-        if (nvert <= T) {
+        if (f->grid_type == 1 || nvert <= T) {
             id = v[0] + side * (v[1] + (d == 3 ? side * v[2] : 0));
         } else {
             uint32_t h = (uint32_t)v[0] * 1u;
@@ -64,14 +86,13 @@ static void level_corners(const orc_field *f, int l, const double *x, int64_t *i
             if (d == 3) h ^= (uint32_t)v[2] * 805459861u;
             id = (int64_t)(h & (uint32_t)(T - 1));
         }
-        idx[c] = id;
+        idx[c] = off + id;
         w[c] = wt;
     }
 }
 
 void orc_field_encode(const orc_field *f, const double *x, double *feat)
 {
-    int64_t T = (int64_t)1 << f->log2T;
     for (int l = 0; l < f->L; ++l) {
         int64_t idx[8];
         double w[8];
@@ -79,7 +100,7 @@ void orc_field_encode(const orc_field *f, const double *x, double *feat)
         for (int j = 0; j < f->F; ++j) {
             double s = 0;
             for (int c = 0; c < (1 << f->dim); ++c)
-                s += w[c] * f->grid[((size_t)l * T + idx[c]) * f->F + j];
+                s += w[c] * f->grid[(size_t)idx[c] * f->F + j];
             feat[l * f->F + j] = s;
         }
     }
@@ -146,13 +167,12 @@ void orc_theta_map(const orc_field *f, const double *raw, double *mu, double *ka
 void orc__field_grid_backward(const orc_field *f, const double *x, const double *dfeat,
                               double *g_grid)
 {
-    int64_t T = (int64_t)1 << f->log2T;
     for (int l = 0; l < f->L; ++l) {
         int64_t idx[8];
         double w[8];
         level_corners(f, l, x, idx, w);
         for (int c = 0; c < (1 << f->dim); ++c)
             for (int j = 0; j < f->F; ++j)
-                g_grid[((size_t)l * T + idx[c]) * f->F + j] += w[c] * dfeat[l * f->F + j];
+                g_grid[(size_t)idx[c] * f->F + j] += w[c] * dfeat[l * f->F + j];
     }
 }

@@ -36,7 +36,8 @@ double orc_u01(uint32_t u);
 typedef struct orc_scene orc_scene;
 orc_scene *orc_scene_create(int dim, int nverts, const double *V, int nprims, const int32_t *P,
                             const uint8_t *bc, int g_kind, const double *g_par, int ng,
-                            int f_kind, const double *f_par, int nf);
+                            int f_kind, const double *f_par, int nf, int h_kind, const double *h_par,
+                            int nh);
 void orc_scene_free(orc_scene *s);
 int orc_scene_nsil(const orc_scene *s);
 double orc_scene_scale(const orc_scene *s);
@@ -63,6 +64,12 @@ int orc_ray_neumann(const orc_scene *s, const double *x, const double *v, double
    side the walk is on (Sec. 4.1, normal convention at Eq. angular_req). */
 int orc_ray_neumann_exit(const orc_scene *s, const double *x, const double *v, double tmax, int skip,
                          double *t);
+/* sample of the Neumann boundary inside the ball B(x, r) for <N> (Sec. 3.2,
+   Eq. wost_estm): returns the chosen Neumann primitive (-1 if none is closer
+   than r), the point z (uniform on it; density 1 / W) and W, the summed
+   length / area of the Neumann primitives closer than r */
+int orc_neumann_sample(const orc_scene *s, const double *x, double r, const uint32_t key[2], uint32_t pid,
+                       uint32_t wid, uint32_t step, double *z, double *W);
 /* winding number (2D) / generalised winding number (3D) */
 double orc_winding(const orc_scene *s, const double *x);
 /* inward unit normal of a primitive */
@@ -89,7 +96,12 @@ typedef struct {
     const double *W2;               /* H x H */
     const double *W3;               /* nout x H, nout = (dim + 2) K + 1 */
     const double *b3;               /* nout */
+    int grid_type;                  /* 0 hash grid (grid: L x 2^log2T x F), 1 dense grid
+                                       (every level dense, level l at entry offset
+                                       sum_{j<l} (N_j + 1)^d; grid: entries x F) */
 } orc_field;
+/* lattice entries of all levels (L 2^log2T for the hash grid) */
+int64_t orc_field_entries(const orc_field *f);
 int orc_field_nout(const orc_field *f);
 int orc_level_res(const orc_field *f, int level);
 void orc_field_encode(const orc_field *f, const double *x, double *feat);
@@ -111,6 +123,8 @@ typedef struct {
     uint64_t seed;
     uint32_t scene_id;
     int nthreads;
+    int rr_depth;        /* Russian roulette from this step on (0 = off) */
+    double rr_survival;  /* survival probability of a roulette step */
 } orc_params;
 
 /* training record exchange layout: 12 doubles
@@ -131,6 +145,13 @@ int orc_point_status(const orc_scene *s, const double *x, double eps, double *va
 double orc_walk(const orc_scene *s, const orc_field *fld, const orc_params *p, uint32_t pid,
                 uint32_t wid, const double *x0, int *steps, int *truncated, double *recs,
                 int max_recs, int *nrec);
+
+/* orc_walk, and with recs: terms (nullable, 2 * max_recs + 1 doubles) receives
+   the suffix-pass inputs of each record k, its step weight w_k and source
+   term S_k at [2k], [2k + 1], and the walk's last value v_n at [2 nrec]. */
+double orc_walk_terms(const orc_scene *s, const orc_field *fld, const orc_params *p, uint32_t pid,
+                      uint32_t wid, const double *x0, int *steps, int *truncated, double *recs,
+                      int max_recs, int *nrec, double *terms);
 
 /* walks [walk_begin, walk_begin + nwalks) of every point (threads over points).
    Adds to sum/sum2 (per point), counts walk-steps and truncated walks.

@@ -20,8 +20,8 @@ struct orc_scene {
     double *V;
     int32_t *P;
     uint8_t *bc;
-    int g_kind, f_kind;
-    double g_par[64], f_par[256];
+    int g_kind, f_kind, h_kind;
+    double g_par[64], f_par[256], h_par[64];
     double scale;      /* bounding-box diagonal */
     double *nin;       /* inward unit normal per primitive */
     /* silhouette elements: 2D = Neumann vertices, 3D = Neumann edges */
@@ -81,6 +81,14 @@ double orc_eval_fn(int kind, const double *p, int d, const double *x)
         return acc;
     }
     case 8: return cosh(p[0] * x[0]) * cos(p[0] * x[1]);
+    case 9: {
+        /* quadratic polynomial c + b.x + sum_i a_ii x_i^2 + a_xy xy + a_xz xz + a_yz yz,
+           p = [c, bx, by, bz, axx, ayy, azz, axy, axz, ayz]; z = 0 in 2D */
+        double X = x[0], Y = x[1], Z = d == 3 ? x[2] : 0.0;
+        return p[0] + p[1] * X + p[2] * Y + p[3] * Z + p[4] * X * X + p[5] * Y * Y + p[6] * Z * Z +
+               p[7] * X * Y + p[8] * X * Z + p[9] * Y * Z;
+    }
+    case 10: return p[0] * atan2(x[1], x[0]) + p[1];   /* polar angle, harmonic in 2D */
     }
     return NAN;
 }
@@ -207,7 +215,8 @@ static int edge_cmp(const void *p, const void *q)
 
 orc_scene *orc_scene_create(int dim, int nverts, const double *V, int nprims, const int32_t *P,
                             const uint8_t *bc, int g_kind, const double *g_par, int ng,
-                            int f_kind, const double *f_par, int nf)
+                            int f_kind, const double *f_par, int nf, int h_kind, const double *h_par,
+                            int nh)
 {
     orc_scene *s = calloc(1, sizeof(orc_scene));
     s->dim = dim;
@@ -221,10 +230,13 @@ orc_scene *orc_scene_create(int dim, int nverts, const double *V, int nprims, co
     memcpy(s->bc, bc, nprims);
     s->g_kind = g_kind;
     s->f_kind = f_kind;
+    s->h_kind = h_kind;
     if (ng > 64) ng = 64;
     if (nf > 256) nf = 256;
+    if (nh > 64) nh = 64;
     for (int i = 0; i < ng; ++i) s->g_par[i] = g_par[i];
     for (int i = 0; i < nf; ++i) s->f_par[i] = f_par[i];
+    for (int i = 0; i < nh; ++i) s->h_par[i] = h_par[i];
 
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int i = 0; i < nverts; ++i)
@@ -478,8 +490,67 @@ int orc_point_status(const orc_scene *s, const double *x, double eps, double *va
     return 0;
 }
 
+/* ---- Neumann boundary sample of <N> (Sec. 3.2, Eq. wost_estm) ----------------
+   Every Neumann primitive closer to x than r is a candidate, with weight its
+   length (2D) or area (3D).  One candidate is chosen with probability
+   weight / W, W the summed weight, by the smallest key -log(u_i) / w_i with
+   u_i in (0, 1] drawn for the primitive itself (Philox counter (point, walk,
+   step, 2^31 | primitive id)): the choice depends on the candidate set only,
+   not on the order the candidates are visited in (Efraimidis & Spirakis
+   2006, weighted sampling with keys).  The point z is uniform on the chosen
+   primitive (counter purpose 96), so its density is 1 / W.  Returns the
+   chosen primitive (-1 when there is no candidate), z and W. */
+static double prim_size(const orc_scene *s, int i)
+{
+    const int32_t *p = s->P + (size_t)i * s->dim;
+    double e1[3], e2[3], c[3];
+    sub(s->dim, vert(s, p[1]), vert(s, p[0]), e1);
+    if (s->dim == 2) return norm(2, e1);
+    sub(3, vert(s, p[2]), vert(s, p[0]), e2);
+    cross3(e1, e2, c);
+    return 0.5 * norm(3, c);
+}
+
+int orc_neumann_sample(const orc_scene *s, const double *x, double r, const uint32_t key[2], uint32_t pid,
+                       uint32_t wid, uint32_t step, double *z, double *W)
+{
+    int best = -1;
+    double best_key = INFINITY, total = 0, q[3];
+    for (int i = 0; i < s->nprims; ++i) {
+        if (s->bc[i] != 1) continue;
+        if (!(prim_closest(s, i, x, q) < r)) continue;
+        double w = prim_size(s, i);
+        uint32_t ctr[4] = {pid, wid, step, 0x80000000u | (uint32_t)i}, o[4];
+        orc_philox4x32_10(ctr, key, o);
+        double u = ((double)(o[0] >> 8) + 1.0) * ldexp(1.0, -24);     /* (0, 1] */
+        double k = -log(u) / w;
+        total += w;
+        if (k < best_key) {
+            best_key = k;
+            best = i;
+        }
+    }
+    *W = total;
+    if (best < 0) return -1;
+    uint32_t ctr[4] = {pid, wid, step, 96u}, o[4];
+    orc_philox4x32_10(ctr, key, o);
+    double u0 = orc_u01(o[0]), u1 = orc_u01(o[1]);
+    const int32_t *p = s->P + (size_t)best * s->dim;
+    if (s->dim == 2) {
+        for (int k = 0; k < 2; ++k) z[k] = (1 - u0) * vert(s, p[0])[k] + u0 * vert(s, p[1])[k];
+    } else {
+        /* uniform on a triangle: barycentrics (1 - sqrt u0, sqrt u0 (1 - u1), sqrt u0 u1) */
+        double su = sqrt(u0);
+        for (int k = 0; k < 3; ++k)
+            z[k] = (1 - su) * vert(s, p[0])[k] + su * (1 - u1) * vert(s, p[1])[k] + su * u1 * vert(s, p[2])[k];
+    }
+    return best;
+}
+
 /* accessors used by the walk */
 int orc__scene_dim(const orc_scene *s) { return s->dim; }
 int orc__scene_fkind(const orc_scene *s) { return s->f_kind; }
+int orc__scene_hkind(const orc_scene *s) { return s->h_kind; }
+double orc__eval_h(const orc_scene *s, const double *x) { return orc_eval_fn(s->h_kind, s->h_par, s->dim, x); }
 double orc__eval_g(const orc_scene *s, const double *x) { return orc_eval_fn(s->g_kind, s->g_par, s->dim, x); }
 double orc__eval_f(const orc_scene *s, const double *x) { return orc_eval_fn(s->f_kind, s->f_par, s->dim, x); }

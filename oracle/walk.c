@@ -14,7 +14,15 @@
  *     Laplacian u = f with G >= 0 the Green function of -Laplacian (a reading,
  *     pinned by manufactured solutions); alpha = 1/2 cancels against the
  *     hemisphere density on Neumann points;
- *   - <N> = 0: zero Neumann flux only;
+ *   - Neumann contribution <N> = G(x, z) h(z) / (alpha p(z)), entering with a
+ *     minus sign as printed: with G >= 0 (the reading above) and h the
+ *     derivative along the normal that points into the domain (the paper's
+ *     normal convention, Sec. 4.1 footnote), Green's second identity on the
+ *     star St gives alpha u(x) = int P u - int_{dSt_N} G h - int_St G f.
+ *     z is drawn on the Neumann boundary inside B(x, r) with density 1 / W
+ *     (orc_neumann_sample); it lies on dSt_N when it faces x: inside B there
+ *     is no silhouette, so no Neumann point there is hidden from x.
+ *     G(x, z) = ln(r / |z - x|) / 2 pi (2D), (1/|z - x| - 1/r) / 4 pi (3D);
  *   - direction: uniform (Sec. 4.1 Eq. for p_u) or, when guided, one-sample
  *     MIS between the vMF mixture decoded by the neural field and uniform
  *     with selection probability c(x) (Sec. 4.4 Eq. mis_pdf); on a Neumann
@@ -23,9 +31,16 @@
  *   - the next point is the first Neumann hit within r, else x + r nu; the
  *     normal at a Neumann point faces the side the walk arrived from
  *     (Sec. 4.1 footnote);
+ *   - Russian roulette once the walk is long (Sec. 6.1 enables it only beyond
+ *     128 steps and states no survival rule; the reading here): from step
+ *     rr_depth on, after the epsilon-shell test, the walk goes on with
+ *     probability q = rr_survival (purpose-97 draw) and its throughput is
+ *     divided by q, else it ends with recursive value 0 -- an unbiased
+ *     estimator of the step's u(x_k).  For the suffix pass that step's weight
+ *     and non-recursive terms carry the same 1/q;
  *   - a hard cap of `maxsteps` moves, after which the walk is closed with g at
- *     the current closest Dirichlet point (reading of the Russian-roulette
- *     remark of Sec. 6.1; counted as truncated).
+ *     the current closest Dirichlet point (counted as truncated; with
+ *     roulette on, a safety net only).
  * Random numbers: Philox4x32-10 with key (seed_lo, seed_hi + scene_id) and
  * counter (point, walk, step, purpose); purpose 0 MIS choice / lobe / 3D vMF,
  * 1 uniform direction, 2 source direction and radius, 3.. 2D vMF retries.
@@ -39,6 +54,8 @@
 
 int orc__scene_dim(const orc_scene *s);
 int orc__scene_fkind(const orc_scene *s);
+int orc__scene_hkind(const orc_scene *s);
+double orc__eval_h(const orc_scene *s, const double *x);
 double orc__eval_g(const orc_scene *s, const double *x);
 double orc__eval_f(const orc_scene *s, const double *x);
 
@@ -122,9 +139,17 @@ double orc_walk(const orc_scene *s, const orc_field *fld, const orc_params *p, u
                 uint32_t wid, const double *x0, int *steps, int *truncated, double *recs,
                 int max_recs, int *nrec)
 {
+    return orc_walk_terms(s, fld, p, pid, wid, x0, steps, truncated, recs, max_recs, nrec, NULL);
+}
+
+double orc_walk_terms(const orc_scene *s, const orc_field *fld, const orc_params *p, uint32_t pid,
+                      uint32_t wid, const double *x0, int *steps, int *truncated, double *recs,
+                      int max_recs, int *nrec, double *terms)
+{
     const int d = orc__scene_dim(s);
     const int K = fld ? fld->K : 0;
     const int has_src = orc__scene_fkind(s) != 0;
+    const int has_flux = orc__scene_hkind(s) != 0;
     const uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32) + p->scene_id};
     const double area = sphere_area(d);
     double x[3] = {0, 0, 0}, n[3] = {0, 0, 0};
@@ -141,6 +166,18 @@ double orc_walk(const orc_scene *s, const orc_field *fld, const orc_params *p, u
             acc += T * term;
             trunc = RD > p->eps;
             break;
+        }
+        /* Russian roulette */
+        double rr = 1.0;
+        if (p->rr_depth > 0 && k >= p->rr_depth) {
+            double u[4];
+            draw(key, pid, wid, (uint32_t)k, 97, u);
+            if (!(u[0] < p->rr_survival)) {
+                term = 0;
+                break;
+            }
+            rr = 1.0 / p->rr_survival;
+            T *= rr;
         }
         double RS;
         orc_closest_silhouette(s, x, &RS);
@@ -160,6 +197,24 @@ double orc_walk(const orc_scene *s, const orc_field *fld, const orc_params *p, u
                 S = -(r * r / (2.0 * d)) * orc__eval_f(s, y);
             }
             acc += T * S;
+        }
+
+        /* Neumann contribution -<N> */
+        if (has_flux) {
+            double z[3], W, Nt = 0;
+            int j = orc_neumann_sample(s, x, r, key, pid, wid, (uint32_t)k, z, &W);
+            if (j >= 0) {
+                double dz[3], nz[3];
+                for (int i = 0; i < d; ++i) dz[i] = z[i] - x[i];
+                double dd = sqrt(vdot(d, dz, dz));
+                orc_inward_normal(s, j, nz);
+                if (dd > 0 && dd < r && vdot(d, dz, nz) < 0) {
+                    double G = d == 2 ? log(r / dd) / (2 * M_PI) : (1 / dd - 1 / r) / (4 * M_PI);
+                    Nt = G * orc__eval_h(s, z) * W / (on_neu ? 0.5 : 1.0);
+                }
+            }
+            S -= Nt;
+            acc -= T * Nt;
         }
 
         /* direction */
@@ -185,7 +240,7 @@ double orc_walk(const orc_scene *s, const orc_field *fld, const orc_params *p, u
         if (on_neu && dn <= 0) {
             /* zero density (Eq. angular_req): the recursive term is 0 and
                the walk's last value is this step's source term */
-            term = S;
+            term = S * rr;
             break;
         }
 
@@ -212,8 +267,8 @@ double orc_walk(const orc_scene *s, const orc_field *fld, const orc_params *p, u
             if (on_neu) memcpy(R + 6, n, sizeof(double) * d);
             R[9] = on_neu;
             R[10] = ptil;
-            info[nr].w = w;
-            info[nr].S = S;
+            info[nr].w = w * rr;
+            info[nr].S = S * rr;
             nr++;
         }
         T *= w;
@@ -237,6 +292,13 @@ double orc_walk(const orc_scene *s, const orc_field *fld, const orc_params *p, u
         }
     }
     if (info) {
+        if (terms) {
+            for (int i = 0; i < nr; ++i) {
+                terms[2 * i] = info[i].w;
+                terms[2 * i + 1] = info[i].S;
+            }
+            terms[2 * nr] = term;
+        }
         /* suffix pass: v_n = terminal value, v_k = w_k v_{k+1} + S_k;
            target of record k is |v_{k+1}| (Sec. 4.1 Eq. guiding_dist) */
         double v = term;

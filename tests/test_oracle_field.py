@@ -114,3 +114,65 @@ def test_theta_map_ranges():
         raw2[K * d + K:K * d + 2 * K] += 3.0
         assert np.allclose(f.theta(raw2)[2], lam)
         assert c == pytest.approx(1 / (1 + np.exp(-raw[-1])))
+
+
+# ---------------------------------------------------------------------------
+# dense-grid encoding (the paper's DenseGrid, Sec. 5.2)
+# ---------------------------------------------------------------------------
+def test_dense_grid_layout_and_affine_reproduction():
+    # every level dense, level l at entry offset sum_{j<l} (N_j + 1)^d; affine
+    # lattice data a.i + b is reproduced exactly at every level, the finest
+    # ones included (which the hash grid would hash)
+    for dim, max_res in ((2, 256), (3, 48)):
+        fp = _field(dim, L=6, base_res=8, max_res=max_res, grid_type=1)
+        f0 = oracle.Field(fp)
+        res = [f0.level_res(l) for l in range(fp.L)]
+        assert res == wi.level_resolutions(fp.L, 8, max_res)
+        sizes = [(n + 1) ** dim for n in res]
+        assert fp.grid.shape == (sum(sizes), fp.F)
+        rng = np.random.default_rng(10 + dim)
+        a = rng.normal(size=dim)
+        b = -0.7
+        grid = np.zeros_like(fp.grid)
+        off = 0
+        for l, n in enumerate(res):
+            side = n + 1
+            idx = np.arange(side ** dim)
+            coords = [(idx // side ** k) % side for k in range(dim)]
+            val = sum(a[k] * coords[k] for k in range(dim)) + b + l     # level-distinct offset
+            grid[off:off + side ** dim, 0] = val
+            grid[off:off + side ** dim, 1] = 3 * val
+            off += side ** dim
+        fp.grid = grid
+        f = oracle.Field(fp)
+        x = rng.uniform(-1.45, 1.45, (60, dim))
+        feat = f.encode(x).reshape(60, fp.L, fp.F)
+        u = (x - fp.lo) / (fp.hi - fp.lo)
+        for l, n in enumerate(res):
+            ref = (u * n) @ a + b + l
+            assert np.allclose(feat[:, l, 0], ref, atol=1e-10)
+            assert np.allclose(feat[:, l, 1], 3 * ref, atol=1e-10)
+
+
+def test_dense_grid_equals_hash_grid_on_its_dense_levels():
+    # the hash grid stores its coarse levels densely at the same lattice
+    # index: copying those levels into a dense grid gives the same features
+    dim = 2
+    fh = _field(dim, seed=4, L=5, log2T=12, base_res=8, max_res=128)
+    fd = _field(dim, seed=4, L=5, log2T=12, base_res=8, max_res=128, grid_type=1)
+    res = wi.level_resolutions(5, 8, 128)
+    off = 0
+    dense_levels = []
+    for l, n in enumerate(res):
+        m = (n + 1) ** dim
+        if m <= 1 << 12:
+            fd.grid[off:off + m] = fh.grid[l, :m]
+            dense_levels.append(l)
+        off += m
+    assert len(dense_levels) >= 2
+    x = np.random.default_rng(3).uniform(-1.4, 1.4, (40, dim))
+    eh = oracle.Field(fh).encode(x).reshape(40, 5, 2)
+    ed = oracle.Field(fd).encode(x).reshape(40, 5, 2)
+    for l in dense_levels:
+        assert np.array_equal(eh[:, l], ed[:, l])
+    assert not np.allclose(eh[:, -1], ed[:, -1])

@@ -9,48 +9,58 @@ import oracle
 import wost_inputs as wi
 
 
-def _setup(dim, seed=0, H=16, K=4):
+def _setup(dim, seed=0, H=16, K=4, grid_type=0):
     sc = wi.half_disk(48, 12) if dim == 2 else wi.slab_box(2)
     lo, hi = sc.padded_bbox()
     fp = oracle.FieldParams(**wi.random_field_params(dim, seed, lo, hi, K=K, L=4, log2T=10, base_res=4,
-                                                     max_res=32, H=H, w_scale=1.5))
+                                                     max_res=32, H=H, w_scale=1.5, grid_type=grid_type))
     fld = oracle.Field(fp)
     S = oracle.Scene(sc)
     prm = oracle.make_params(seed=seed + 1, guided=1)
     recs = []
     for wid in range(30):
         recs.append(oracle.walk(S, prm, 0, wid, np.array([0.1, 0.2, 0.5][:dim]), field=fld, records=True)["records"])
-    recs = np.concatenate(recs)[:60]
+    recs = np.concatenate(recs)
+    # 50 records in walk order and up to 10 at Neumann points
+    recs = np.concatenate([recs[:50], recs[50:][recs[50:, 9] == 1][:10]])
     assert (recs[:, 9] == 1).any()
     return fp, recs
 
 
-@pytest.mark.parametrize("dim,c_mode", [(2, 0), (3, 0), (2, 1)])
-def test_gradient_matches_central_differences(dim, c_mode):
-    fp, recs = _setup(dim)
+@pytest.mark.parametrize("dim,c_mode,grid_type", [(2, 0, 0), (3, 0, 0), (2, 1, 0), (2, 0, 1), (3, 0, 1)])
+def test_gradient_matches_central_differences(dim, c_mode, grid_type):
+    fp, recs = _setup(dim, grid_type=grid_type)
     f = oracle.Field(fp)
     loss0, grads, pg0 = f.train_loss(recs, c_mode=c_mode, c_fixed=0.7)
     rng = np.random.default_rng(1)
     names = ["grid", "W1", "W2", "W3", "b3"]
-    checked = 0
+    checked = skipped = 0
     for name, g in zip(names, grads):
         arr = getattr(fp, name)
         flat = arr.reshape(-1)
         cand = np.nonzero(np.abs(g.reshape(-1)) > 1e-8 * np.abs(g).max())[0]
-        for j in rng.choice(cand, size=min(8, len(cand)), replace=False):
+        def fd5(j, h):
             # five-point central difference: truncation O(h^4), roundoff ~ eps |loss| / h
-            h = 1e-4 * max(1.0, abs(flat[j]))
             old = flat[j]
             L = {}
             for k in (-2, -1, 1, 2):
                 flat[j] = old + k * h
                 L[k] = oracle.Field(fp).train_loss(recs, c_mode=c_mode, c_fixed=0.7, frozen_pg=pg0, grad=False)[0]
             flat[j] = old
-            fd = (-L[2] + 8 * L[1] - 8 * L[-1] + L[-2]) / (12 * h)
+            return (-L[2] + 8 * L[1] - 8 * L[-1] + L[-2]) / (12 * h)
+        for j in rng.choice(cand, size=min(8, len(cand)), replace=False):
+            h = 1e-4 * max(1.0, abs(flat[j]))
             tol_round = 100 * np.finfo(float).eps * abs(loss0) / h
+            fd, fd4 = fd5(j, h), fd5(j, h / 4)
+            # a stencil that straddles a ReLU kink (some record's hidden
+            # pre-activation within a few h of zero) is not smooth: the two
+            # step sizes disagree, and that entry is skipped
+            if abs(fd - fd4) > 1e-6 * abs(fd4) + 8 * tol_round:
+                skipped += 1
+                continue
             assert g.reshape(-1)[j] == pytest.approx(fd, rel=1e-6, abs=tol_round), (name, j)
             checked += 1
-    assert checked >= 30
+    assert checked >= 30 and skipped <= 4, (checked, skipped)
 
 
 def test_raw_output_gradient_is_the_papers_estimator():

@@ -32,6 +32,8 @@ FN_INV_DIST = 5    # 1/|x - c|, c = params[0:3] (harmonic in 3D)
 FN_LOG_DIST = 6    # log|x - c|, c = params[0:2] (harmonic in 2D)
 FN_GAUSS_SUM = 7   # sum_i A_i exp(-|x-p_i|^2/(2 s^2)); params = [n, s, A_1, p_1(3), ...]
 FN_COSH_COS = 8    # cosh(a x) cos(a y), a = params[0]
+FN_POLY2 = 9       # c + b.x + sum a_ij x_i x_j; params = [c, bx, by, bz, axx, ayy, azz, axy, axz, ayz]
+FN_ATAN2 = 10      # params[0] * atan2(y, x) + params[1] (polar angle, harmonic in 2D)
 
 BC_DIRICHLET = 0
 BC_NEUMANN = 1
@@ -55,7 +57,7 @@ class Scene:
     bc: np.ndarray             # (np,) uint8, BC_DIRICHLET / BC_NEUMANN
     g: Fn                      # Dirichlet data
     f: Fn = dataclasses.field(default_factory=Fn)   # source term (Laplacian u = f)
-    h: Fn = dataclasses.field(default_factory=Fn)   # Neumann flux (zero only)
+    h: Fn = dataclasses.field(default_factory=Fn)   # Neumann flux du/dn, n pointing into the domain
     exact: Optional[Fn] = None  # closed-form solution when one exists
     scene_id: int = 0
 
@@ -97,6 +99,14 @@ def eval_fn(fn: Fn, x: np.ndarray) -> np.ndarray:
         return np.log(np.linalg.norm(x - c, axis=1))
     if k == FN_COSH_COS:
         return np.cosh(p[0] * x[:, 0]) * np.cos(p[0] * x[:, 1])
+    if k == FN_POLY2:
+        X, Y = x[:, 0], x[:, 1]
+        Z = x[:, 2] if x.shape[1] == 3 else np.zeros(len(x))
+        q = list(p) + [0.0] * (10 - len(p))
+        return (q[0] + q[1] * X + q[2] * Y + q[3] * Z + q[4] * X * X + q[5] * Y * Y + q[6] * Z * Z
+                + q[7] * X * Y + q[8] * X * Z + q[9] * Y * Z)
+    if k == FN_ATAN2:
+        return p[0] * np.arctan2(x[:, 1], x[:, 0]) + (p[1] if len(p) > 1 else 0.0)
     if k == FN_GAUSS_SUM:
         n, s = int(p[0]), p[1]
         out = np.zeros(len(x))
@@ -164,6 +174,23 @@ def half_disk(narc: int = 64, nflat: int = 16, g: Optional[Fn] = None) -> Scene:
     return Scene("half_disk", 2, v, prims, bc, g, exact=g)
 
 
+def half_disk_flux(narc: int = 64, nflat: int = 16, poisson: bool = False) -> Scene:
+    """Upper half disk with a nonzero Neumann flux on the flat edge y = 0
+    (normal (0, 1) into the domain).  Laplace: u = x^2 - y^2 + x y + y, so
+    h = du/dy(y = 0) = 1 + x.  Poisson (f = 4): u = x^2 + y^2 + y, h = 1."""
+    sc = half_disk(narc, nflat)
+    if poisson:
+        u = Fn(FN_POLY2, [0, 0, 1, 0, 1, 1, 0, 0, 0, 0])
+        sc.f = Fn(FN_CONST, [4.0])
+        sc.h = Fn(FN_CONST, [1.0])
+    else:
+        u = Fn(FN_POLY2, [0, 0, 1, 0, 1, -1, 0, 1, 0, 0])
+        sc.h = Fn(FN_POLY2, [1, 1, 0, 0, 0, 0, 0, 0, 0, 0])
+    sc.g = sc.exact = u
+    sc.name = "half_disk_flux"
+    return sc
+
+
 def rectangle_channel(nx: int = 16, ny: int = 8, a: float = math.pi) -> Scene:
     """[-1,1] x [0,1]: the edges y = 0 and y = 1 are zero-flux Neumann, x = +-1
     Dirichlet with g = cosh(a x) cos(a y), exact for a = pi (dg/dy = 0 on both
@@ -184,6 +211,27 @@ def rectangle_channel(nx: int = 16, ny: int = 8, a: float = math.pi) -> Scene:
     bc[nx + ny: 2 * nx + ny] = BC_NEUMANN
     g = Fn(FN_COSH_COS, [a])
     return Scene("channel2d", 2, v, _closed_loop(n), bc, g, exact=g)
+
+
+def annulus_sector(r_in: float = 0.9, r_out: float = 1.0, theta_max: float = 0.95 * math.pi,
+                   narc: int = 1024) -> Scene:
+    """The thin annulus sector r_in < |x| < r_out, 0 < angle < theta_max:
+    zero-flux Neumann arcs, Dirichlet radial ends with g = angle / theta_max,
+    the polar angle being harmonic with zero normal derivative on circles
+    (exact for the curved domain; the polygon's chords put a small error on
+    it).  The inner circle's silhouette keeps the star radius near the
+    annulus width, so walks from the middle take hundreds of steps."""
+    th = theta_max * np.arange(narc + 1) / narc
+    outer = np.stack([r_out * np.cos(th), r_out * np.sin(th)], 1)          # CCW, domain on the left
+    inner = np.stack([r_in * np.cos(th[::-1]), r_in * np.sin(th[::-1])], 1)  # CW back to angle 0
+    v = np.concatenate([outer, inner], 0)
+    n = len(v)
+    prims = _closed_loop(n)
+    bc = np.ones(n, np.uint8)
+    bc[narc] = BC_DIRICHLET          # outer end -> inner end at theta_max
+    bc[n - 1] = BC_DIRICHLET         # inner start -> outer start at angle 0
+    g = Fn(FN_ATAN2, [1.0 / theta_max, 0.0])
+    return Scene("annulus_sector", 2, v, prims, bc, g, exact=g)
 
 
 # ---- 3D scenes --------------------------------------------------------------
@@ -457,6 +505,18 @@ def slab_box(n: int = 4) -> Scene:
     return Scene("slab_box", 3, verts, tris.astype(np.int32), np.array(bcs, np.uint8), g, exact=g)
 
 
+def slab_box_flux(n: int = 3) -> Scene:
+    """The slab box with a nonzero flux through both Neumann planes:
+    u = x^2 - y^2 + z + x z, du/dz = 1 + x; the normal into the domain is +z
+    on z = 0 and -z on z = 1, so h = (1 + x)(1 - 2 z)."""
+    sc = slab_box(n)
+    u = Fn(FN_POLY2, [0, 0, 0, 1, 1, -1, 0, 0, 1, 0])
+    sc.g = sc.exact = u
+    sc.h = Fn(FN_POLY2, [1, 1, 0, -2, 0, 0, 0, 0, -2, 0])
+    sc.name = "slab_box_flux"
+    return sc
+
+
 def sphere_dirichlet(subdiv: int = 3, g: Optional[Fn] = None) -> Scene:
     """Unit icosphere, all Dirichlet (g = 1/|x - c| with c outside is exact)."""
     v, f = icosphere(subdiv)
@@ -613,9 +673,22 @@ def subsample(pts: np.ndarray, n: int, seed: int = 0) -> np.ndarray:
 
 # ---- neural-field parameters for tests (exchange layout) ---------------------
 
+def level_resolutions(L: int, base_res: int, max_res: int):
+    """N_l = floor(N_min b^l), b such that N_{L-1} = N_max (both encodings)."""
+    if L == 1:
+        return [base_res]
+    b = math.exp((math.log(max_res) - math.log(base_res)) / (L - 1))
+    return [int(math.floor(base_res * b ** l + 1e-6)) for l in range(L)]
+
+
+def dense_grid_entries(dim: int, L: int, base_res: int, max_res: int) -> int:
+    """Lattice entries of the dense-grid encoding: sum_l (N_l + 1)^d."""
+    return sum((n + 1) ** dim for n in level_resolutions(L, base_res, max_res))
+
+
 def random_field_params(dim: int, seed: int, lo, hi, K: int = 8, L: int = 16, log2T: int = 16,
                         F: int = 2, H: int = 64, base_res: int = 16, max_res: Optional[int] = None,
-                        grid_scale: float = 0.5, w_scale: float = 1.0):
+                        grid_scale: float = 0.5, w_scale: float = 1.0, grid_type: int = 0):
     """Seeded field parameters in the exchange layout used by both
     implementations: grid (L, 2^log2T, F), W1 (H, L*F), W2 (H, H),
     W3 (nout, H), b3 (nout) with nout = (dim + 2) K + 1.  Returned as a dict
@@ -626,14 +699,17 @@ def random_field_params(dim: int, seed: int, lo, hi, K: int = 8, L: int = 16, lo
     T = 1 << log2T
     nin = L * F
     nout = (dim + 2) * K + 1
-    grid = rng.uniform(-grid_scale, grid_scale, (L, T, F))
+    if grid_type == 1:
+        grid = rng.uniform(-grid_scale, grid_scale, (dense_grid_entries(dim, L, base_res, max_res), F))
+    else:
+        grid = rng.uniform(-grid_scale, grid_scale, (L, T, F))
     W1 = rng.uniform(-1, 1, (H, nin)) * w_scale * math.sqrt(6.0 / nin)
     W2 = rng.uniform(-1, 1, (H, H)) * w_scale * math.sqrt(6.0 / H)
     W3 = rng.uniform(-1, 1, (nout, H)) * w_scale * math.sqrt(6.0 / H) * 0.5
     b3 = rng.normal(size=nout) * 0.5
     return dict(dim=dim, K=K, L=L, log2T=log2T, F=F, H=H, base_res=base_res, max_res=max_res,
                 lo=np.asarray(lo, float), hi=np.asarray(hi, float),
-                grid=grid, W1=W1, W2=W2, W3=W3, b3=b3)
+                grid=grid, W1=W1, W2=W2, W3=W3, b3=b3, grid_type=grid_type)
 
 
 def round_to_bf16(a: np.ndarray) -> np.ndarray:
