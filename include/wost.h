@@ -3,7 +3,7 @@
  *
  * C ABI of the data-parallel hot path of "Guiding-Based Importance Sampling
  * for Walk on Stars" (arXiv 2410.18944): batched walk-on-stars (WoSt) walks
- * for the Poisson problem with mixed Dirichlet / zero-flux Neumann boundary
+ * for the Poisson problem with mixed Dirichlet / Neumann boundary
  * (Sec. 3.1, Eq. linear_elliptic; estimator Sec. 3.2 Eq. wost_estm and its
  * reparameterisation Sec. 4.1), with optional guided direction sampling from
  * a von Mises-Fisher mixture decoded by a hash-grid + MLP neural field
@@ -25,6 +25,10 @@
  *    CUDA device.  Work is enqueued on wost_exec.stream (NULL = legacy
  *    default stream) and the call synchronises that stream before returning
  *    unless stated otherwise.
+ *  - a scene, field or batch belongs to the CUDA device that was current
+ *    when it was created; every call that uses it first checks that this
+ *    device is current and otherwise returns WOST_ERR_INVALID_ARG without
+ *    launching anything.
  *  - geometry is stored in FP32, per-point accumulators in FP64.
  *  - there is no CPU fallback: without a usable CUDA device every call that
  *    needs one returns WOST_ERR_CUDA.
@@ -46,7 +50,7 @@ typedef enum {
     WOST_ERR_CUDA = 3,         /* CUDA runtime error (message has details) */
     WOST_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
     WOST_ERR_OOM = 5,          /* device allocation failed */
-    WOST_ERR_UNSUPPORTED = 6   /* valid but not implemented (e.g. h != 0) */
+    WOST_ERR_UNSUPPORTED = 6   /* valid but not supported by this build (e.g. a field shape) */
 } wost_status;
 
 /* Analytic data functions g (Dirichlet), f (source), h (Neumann flux).
@@ -55,7 +59,10 @@ typedef enum {
      3 x^2 - y^2       4 |x|^2                 5 1/|x - p[0:3]|
      6 log|x - p[0:2]| 7 sum_i A_i exp(-|x - c_i|^2 / (2 s^2)),
                          p = [n, s, A_1, c_1(3), A_2, c_2(3), ...], n <= 8
-     8 cosh(p0 x) cos(p0 y) */
+     8 cosh(p0 x) cos(p0 y)
+     9 c + b.x + a_xx x^2 + a_yy y^2 + a_zz z^2 + a_xy x y + a_xz x z + a_yz y z,
+                         p = [c, bx, by, bz, a_xx, a_yy, a_zz, a_xy, a_xz, a_yz] (z = 0 in 2D)
+    10 p0 atan2(y, x) + p1 (polar angle) */
 typedef struct {
     int32_t kind;
     int32_t nparams;
@@ -75,7 +82,8 @@ typedef struct {
     const uint8_t *bc;         /* host, nprims */
     wost_fn g;                 /* Dirichlet data */
     wost_fn f;                 /* source, Laplacian u = f */
-    wost_fn h;                 /* Neumann flux: must be zero (kind 0) */
+    wost_fn h;                 /* Neumann flux du/dn, n the normal pointing into the domain
+                                  (kind 0: zero flux, the <N> term is skipped) */
     uint32_t scene_id;         /* folded into the random-number key */
 } wost_scene_desc;
 
@@ -85,11 +93,12 @@ typedef struct wost_field wost_field;
 /* Neural field of the guiding distribution (Sec. 5.2): L levels of a hash
    grid (2^log2_table entries x F features, FP32 master + FP16 copy), MLP
    (L F) -> H -> H -> (d + 2) K + 1 with ReLU, BF16 operands, FP32
-   accumulation.  Fixed in this build: F = 2, L * F = 32, H = 64, K = 8.
+   accumulation.  Fixed in this build: F = 2, L * F = 32, H = 64; K = 1..8
+   lobes (8 by default; the lobe-count ablation of Sec. 6.3 uses 4 and 8).
    Positions are mapped to [0,1]^d by the box [lo, hi]. */
 typedef struct {
     int32_t dim;
-    int32_t K;                 /* lobes (8) */
+    int32_t K;                 /* lobes (1..8, default 8) */
     int32_t levels;            /* L (16) */
     int32_t log2_table;        /* log2 of entries per level */
     int32_t features;          /* F (2) */
@@ -100,6 +109,12 @@ typedef struct {
     float lr_grid, lr_mlp;     /* Adam learning rates */
     float beta1, beta2, adam_eps;
     float e_sel;               /* selection-loss fraction e (0.2, Sec. 4.4) */
+    int32_t grid_type;         /* 0 hash grid: every level has 2^log2_table entries, dense
+                                  indexing where (N_l + 1)^d fits, else the spatial hash;
+                                  exchange layout grid [L][2^log2_table][F].
+                                  1 dense grid (the encoding of Sec. 5.2): every level dense
+                                  with its own (N_l + 1)^d vertices (x fastest), the levels one
+                                  after the other; exchange layout grid [entries][F] */
 } wost_field_desc;
 
 /* Execution options of a solve. */
@@ -132,6 +147,15 @@ typedef struct {
                                   record once); one wost_train_step / wost_train_grad call takes
                                   the stratum o = (t * 2654435761) mod k, t the field's Adam step
                                   count before the step */
+    int32_t rr_depth;          /* Russian roulette (Sec. 6.1: only for walks longer than 128 steps)
+                                  from this step on: 0 = off (walks end at the maxsteps cap); a
+                                  step k >= rr_depth goes on with probability rr_survival and
+                                  divides the throughput by it, else the walk ends with value 0 */
+    float rr_survival;         /* in (0, 1]; default 0.995 */
+    int64_t wait_ns;           /* guided walks: limit in nanoseconds of every device-side wait of
+                                  one warp on others (a decode tile filled, decoded or consumed);
+                                  0 = 2 s.  A wait that runs out ends the launch and the call
+                                  returns WOST_ERR_TIMEOUT; the device stays usable */
 } wost_exec;
 
 typedef struct {
@@ -166,6 +190,8 @@ void wost_field_desc_defaults(wost_field_desc *desc, int32_t dim);
    uploads them.  WOST_ERR_ILL_POSED if there is no Dirichlet primitive. */
 wost_status wost_create_scene(const wost_scene_desc *desc, wost_scene **out);
 wost_status wost_destroy_scene(wost_scene *scene);
+/* the CUDA device the scene belongs to (current at wost_create_scene) */
+wost_status wost_scene_device(const wost_scene *scene, int32_t *device);
 /* padded bounding box (5% of the extent on each side) for the field box */
 wost_status wost_scene_bbox(const wost_scene *scene, double lo[3], double hi[3]);
 
@@ -194,6 +220,9 @@ wost_status wost_field_set_params(wost_field *field, const float *grid, const fl
                                   const float *W2, const float *W3, const float *b3);
 wost_status wost_field_get_params(const wost_field *field, float *grid, float *W1, float *W2,
                                   float *W3, float *b3);
+/* Lattice entries of the field's grid, all levels (L 2^log2_table for the
+   hash grid, sum_l (N_l + 1)^d for the dense grid). */
+wost_status wost_field_grid_entries(const wost_field *field, int64_t *entries);
 /* Raw network outputs (nout floats per point, host-or-device per exec) for
    npoints points (npoints * dim doubles): hash-grid encoding + MLP on tensor
    cores, the decode used inside the guided walk. */
@@ -213,6 +242,12 @@ wost_status wost_train_records(wost_field *field, const float *records, int64_t 
                                const wost_exec *exec);
 /* Copies up to cap records of the buffer to host memory; *n = count. */
 wost_status wost_get_records(const wost_field *field, float *records, int64_t cap, int64_t *n);
+/* The mean surrogate loss of wost_train_grad alone (the same fused kernel:
+   forward recomputed from the records on tensor cores, no backward pass,
+   gradient buffers untouched).  out_loss: one float, host memory, or device
+   memory with exec->out_on_device (then the call only enqueues on
+   exec->stream and does not synchronise). */
+wost_status wost_train_loss(wost_field *field, const wost_exec *exec, float *out_loss);
 /* Loss and gradients without the Adam update: grads in the exchange layout
    (host or device; nullable each), from the same fused kernel as
    wost_train_step: the forward is recomputed from the records and the
@@ -234,6 +269,21 @@ wost_status wost_query_silhouette(wost_scene *scene, const double *points, int64
 wost_status wost_query_ray(wost_scene *scene, const double *org, const double *dir,
                            const double *tmax, const int32_t *skip, int64_t n,
                            int32_t *out_prim, float *out_t);
+/* The cast a walk step makes (Sec. 3.2: the next point is the first hit on
+   the star's Neumann boundary within r, else x + r nu), for testing it on its
+   own.  Only primitives the ray leaves the domain through count (direction
+   against the inward normal): inside a closed boundary the first crossing is
+   an exit.  Crossings count from t > -b and within about b of the primitive,
+   b = 16 * 2^-24 * (bounding-box diagonal), so a start point rounded a hair
+   outside the boundary next to a vertex still leaves through the neighbour.
+   org / dir / tmax are rounded to FP32 as a walk holds them; a winner whose
+   FP32 parameter lies within b of tmax is re-tested in FP64 against the FP32
+   tmax.  skip[i]: primitive id the ray starts on (-1 none, nullable array).
+   Outputs: the primitive id (-1 if none within tmax) and its FP32 parameter
+   (+inf if none).  Host arrays. */
+wost_status wost_query_ray_exit(wost_scene *scene, const double *org, const double *dir,
+                                const double *tmax, const int32_t *skip, int64_t n,
+                                int32_t *out_prim, float *out_t);
 /* vMF mixture: pdf at directions given identical parameters (mu K x d,
    kappa K, lambda K per row) and one guided sample per row from Philox
    counters (point, walk, step) with the walk's key; all host arrays. */
@@ -322,6 +372,8 @@ wost_status wost_solve_batch(int32_t njobs, const wost_job *jobs, int32_t guided
      npoints       at most WOST_STATIC_MAX_POINTS, else WOST_ERR_INVALID_ARG
      stream        cudaStream_t (NULL = default); synchronised before return
      out_walk_steps (nullable, host) walk-steps of the solve
+   The scene must belong to the current device (WOST_ERR_INVALID_ARG
+   otherwise, before any launch).
    The first call on a device looks up the array's device address with
    cudaGetSymbolAddress (make it before any stream capture).  Every call
    reuses the same array and clears what must start at zero; calls whose GPU
@@ -333,6 +385,19 @@ wost_status wost_solve_plain_static(wost_scene *scene, const double *points_dev,
                                     int64_t *out_walk_steps);
 
 /* ---- diagnostics ---------------------------------------------------------- */
+/* The failure path of the bounded device-side waits, without a fault: one
+   warp waits (the walk kernels' bounded wait) on a shared-memory mbarrier
+   that gets its arrival only if `arrive` != 0.  Without it the wait runs out
+   after limit_ns (0 < limit_ns <= 1e10) and the call returns
+   WOST_ERR_TIMEOUT; the device stays usable.  With it the call returns
+   WOST_OK. */
+wost_status wost_diag_wait(int64_t limit_ns, int32_t arrive);
+/* Records `device` as the device the scene belongs to, without moving any of
+   its data.  For tests of the device check on one-GPU machines: with a
+   device other than the current one, every later call on the scene returns
+   WOST_ERR_INVALID_ARG before any launch; rebinding to the true device
+   restores it. */
+wost_status wost_diag_scene_rebind(wost_scene *scene, int32_t device);
 /* D[128 x N] = A[128 x K] B[N x K]^T (host float arrays, row-major) through
    the library's tensor-core path (BF16 operands, FP32 accumulation); a_mn /
    b_mn select K-major (0) or MN-major (1) shared-memory storage.  N in

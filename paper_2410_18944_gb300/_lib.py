@@ -37,7 +37,7 @@ class FieldDesc(C.Structure):
                 ("features", C.c_int32), ("hidden", C.c_int32), ("base_res", C.c_int32), ("max_res", C.c_int32),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("seed", C.c_uint64),
                 ("lr_grid", C.c_float), ("lr_mlp", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
-                ("adam_eps", C.c_float), ("e_sel", C.c_float)]
+                ("adam_eps", C.c_float), ("e_sel", C.c_float), ("grid_type", C.c_int32)]
 
 
 class Exec(C.Structure):
@@ -46,7 +46,8 @@ class Exec(C.Structure):
                 ("reflect", C.c_int32), ("train", C.c_int32), ("train_until_wpp", C.c_int32),
                 ("max_train_records", C.c_int64), ("walk_begin", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("guided_kernel", C.c_int32), ("wavefront_slots", C.c_int32),
-                ("train_samples", C.c_int64)]
+                ("train_samples", C.c_int64), ("rr_depth", C.c_int32), ("rr_survival", C.c_float),
+                ("wait_ns", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -90,6 +91,8 @@ SIGNATURES = {
     "wost_create_scene": (C.c_int, [C.POINTER(SceneDesc), C.POINTER(_vp)]),
     "wost_destroy_scene": (C.c_int, [_vp]),
     "wost_scene_bbox": (C.c_int, [_vp, _dp, _dp]),
+    "wost_scene_device": (C.c_int, [_vp, _i32p]),
+    "wost_diag_scene_rebind": (C.c_int, [_vp, C.c_int32]),
     "wost_solve": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int32, C.c_double, C.c_int32, C.c_int32,
                              _vp, _vp, C.POINTER(Stats), C.POINTER(Exec)]),
     "wost_create_field": (C.c_int, [C.POINTER(FieldDesc), C.POINTER(_vp)]),
@@ -97,17 +100,21 @@ SIGNATURES = {
     "wost_field_set_params": (C.c_int, [_vp, _fp, _fp, _fp, _fp, _fp]),
     "wost_field_get_params": (C.c_int, [_vp, _fp, _fp, _fp, _fp, _fp]),
     "wost_field_decode": (C.c_int, [_vp, _vp, C.c_int64, _vp, C.POINTER(Exec)]),
+    "wost_field_grid_entries": (C.c_int, [_vp, _i64p]),
     "wost_train_step": (C.c_int, [_vp, _vp, C.POINTER(Exec), _fp]),
     "wost_train_records": (C.c_int, [_vp, _vp, C.c_int64, C.POINTER(Exec)]),
     "wost_get_records": (C.c_int, [_vp, _fp, C.c_int64, _i64p]),
     "wost_train_grad": (C.c_int, [_vp, C.POINTER(Exec), _fp, _fp, _fp, _fp, _fp, _fp]),
+    "wost_train_loss": (C.c_int, [_vp, C.POINTER(Exec), _vp]),
     "wost_query_closest": (C.c_int, [_vp, _dp, C.c_int64, _i32p, _fp]),
     "wost_query_silhouette": (C.c_int, [_vp, _dp, C.c_int64, _i64p, _fp]),
     "wost_query_ray": (C.c_int, [_vp, _dp, _dp, _dp, _i32p, C.c_int64, _i32p, _fp]),
+    "wost_query_ray_exit": (C.c_int, [_vp, _dp, _dp, _dp, _i32p, C.c_int64, _i32p, _fp]),
     "wost_mixture_eval": (C.c_int, [C.c_int32, C.c_int32, _fp, _fp, _fp, _fp, C.c_int64, _fp]),
     "wost_mixture_sample": (C.c_int, [C.c_int32, C.c_int32, _fp, _fp, _fp, _u32p, C.c_uint64, C.c_uint32,
                                       C.c_int64, _fp, _fp]),
     "wost_diag_umma": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _fp, _fp, _fp]),
+    "wost_diag_wait": (C.c_int, [C.c_int64, C.c_int32]),
     "wost_batch_create": (C.c_int, [C.c_int32, C.POINTER(Job), C.c_int32, C.POINTER(Exec), C.POINTER(_vp)]),
     "wost_batch_run": (C.c_int, [_vp, _vp, C.POINTER(Stats)]),
     "wost_batch_info_get": (C.c_int, [_vp, C.POINTER(BatchInfo)]),

@@ -79,6 +79,11 @@ class Scene:
 
     __del__ = close
 
+    def device(self):
+        d = C.c_int32()
+        check(L.load().wost_scene_device(self._h, C.byref(d)))
+        return d.value
+
     def bbox(self):
         lo, hi = np.zeros(3), np.zeros(3)
         check(L.load().wost_scene_bbox(self._h, lo.ctypes.data_as(L._dp), hi.ctypes.data_as(L._dp)))
@@ -103,7 +108,9 @@ class Scene:
                                              d.ctypes.data_as(L._fp)))
         return idx, d
 
-    def query_ray(self, org, dirs, tmax, skip=None):
+    def query_ray(self, org, dirs, tmax, skip=None, exit_only=False):
+        """wost_query_ray (first hit of either orientation) or, with
+        ``exit_only``, wost_query_ray_exit (the cast of a walk step)."""
         o = np.ascontiguousarray(org, np.float64)
         v = np.ascontiguousarray(dirs, np.float64)
         n = len(o)
@@ -111,9 +118,10 @@ class Scene:
         s = None if skip is None else np.ascontiguousarray(np.broadcast_to(np.asarray(skip, np.int32), (n,)))
         idx = np.zeros(n, np.int32)
         th = np.zeros(n, np.float32)
-        check(L.load().wost_query_ray(self._h, o.ctypes.data_as(L._dp), v.ctypes.data_as(L._dp),
-                                      t.ctypes.data_as(L._dp), s.ctypes.data_as(L._i32p) if s is not None else None,
-                                      n, idx.ctypes.data_as(L._i32p), th.ctypes.data_as(L._fp)))
+        fn = L.load().wost_query_ray_exit if exit_only else L.load().wost_query_ray
+        check(fn(self._h, o.ctypes.data_as(L._dp), v.ctypes.data_as(L._dp), t.ctypes.data_as(L._dp),
+                 s.ctypes.data_as(L._i32p) if s is not None else None, n, idx.ctypes.data_as(L._i32p),
+                 th.ctypes.data_as(L._fp)))
         return idx, th
 
 
@@ -138,6 +146,9 @@ class Field:
         h = C.c_void_p()
         check(lib.wost_create_field(C.byref(d), C.byref(h)))
         self._h = h
+        n = C.c_int64()
+        check(lib.wost_field_grid_entries(h, C.byref(n)))
+        self.entries = n.value
 
     def close(self):
         if getattr(self, "_h", None):
@@ -149,7 +160,8 @@ class Field:
     def shapes(self):
         d = self.desc
         nin = d.levels * d.features
-        return dict(grid=(d.levels, self.T, d.features), W1=(d.hidden, nin), W2=(d.hidden, d.hidden),
+        grid = (d.levels, self.T, d.features) if d.grid_type == 0 else (self.entries, d.features)
+        return dict(grid=grid, W1=(d.hidden, nin), W2=(d.hidden, d.hidden),
                     W3=(self.nout, d.hidden), b3=(self.nout,))
 
     def set_params(self, grid, W1, W2, W3, b3):

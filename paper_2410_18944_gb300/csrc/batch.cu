@@ -111,6 +111,7 @@ using namespace wost;
 
 struct wost_batch {
     int dim = 0;
+    int device = -1;                 // the device of its jobs' scenes and fields
     bool guided = false, record = false;
     wost_exec ex{};
     std::vector<wost_job> jobs;
@@ -169,6 +170,7 @@ struct wost_batch {
             g.o.scratch = L.record ? scratch.as<float>() : nullptr;
             g.o.scratch_steps = scratch_steps;
             g.o.flush_polls = polls_;
+            g.o.wait_ns = ex.wait_ns > 0 ? (unsigned long long)ex.wait_ns : kWaitNs;
             g.o.err = b.err;
             g.o.stat = b.stat;
             if (dim == 2) batch_guided_kernel<2><<<num_sms(), kWsThreads, kBatchGuidedSmem, st>>>(g);
@@ -269,6 +271,10 @@ namespace {
 
 wost_status validate(int32_t njobs, const wost_job *jobs, int32_t guided, const wost_exec &ex) {
     if (njobs <= 0 || !jobs) { set_error("wost_batch_create: no jobs"); return WOST_ERR_INVALID_ARG; }
+    if (ex.rr_depth < 0 || (ex.rr_depth > 0 && !(ex.rr_survival > 0.f && ex.rr_survival <= 1.f))) {
+        set_error("wost_batch_create: rr_depth must be >= 0 and rr_survival in (0, 1]");
+        return WOST_ERR_INVALID_ARG;
+    }
     const int dim = jobs[0].scene ? jobs[0].scene->dim : 0;
     std::unordered_set<const wost_field *> fields;
     for (int j = 0; j < njobs; ++j) {
@@ -276,6 +282,7 @@ wost_status validate(int32_t njobs, const wost_job *jobs, int32_t guided, const 
         std::string at = "wost_batch_create: job " + std::to_string(j) + ": ";
         if (!J.scene) { set_error(at + "null scene"); return WOST_ERR_INVALID_ARG; }
         if (J.scene->dim != dim) { set_error(at + "all jobs of a batch must have the same dimension"); return WOST_ERR_INVALID_ARG; }
+        if (wost_status dc = check_device(J.scene->device, "wost_batch_create (scene)")) return dc;
         if (J.npoints < 0 || J.npoints > (int64_t)UINT32_MAX || J.nwalks <= 0 || !(J.eps > 0) || J.maxsteps < 0) {
             set_error(at + "invalid npoints / nwalks / eps / maxsteps");
             return WOST_ERR_INVALID_ARG;
@@ -284,6 +291,7 @@ wost_status validate(int32_t njobs, const wost_job *jobs, int32_t guided, const 
         if (guided) {
             if (!J.field) { set_error(at + "a guided batch needs a field per job"); return WOST_ERR_INVALID_ARG; }
             if (J.field->desc.dim != dim) { set_error(at + "field dimension differs from the scene"); return WOST_ERR_INVALID_ARG; }
+            if (wost_status dc = check_device(J.field->device, "wost_batch_create (field)")) return dc;
             if (ex.train && !fields.insert(J.field).second) {
                 set_error(at + "jobs that train need distinct fields");
                 return WOST_ERR_INVALID_ARG;
@@ -322,6 +330,8 @@ wost_status build_plan(wost_batch *p) {
         d.eps64 = J.eps;
         d.key0 = (uint32_t)J.seed;
         d.key1 = (uint32_t)(J.seed >> 32) + J.scene->scene_id;
+        d.rr_depth = p->ex.rr_depth;
+        d.rr_q = p->ex.rr_survival;
         d.out_mean = J.out_mean;
         d.out_var = J.out_var;
         if (p->guided) d.f = J.field->dev();
@@ -438,6 +448,7 @@ extern "C" wost_status wost_batch_create(int32_t njobs, const wost_job *jobs, in
     if (rc != WOST_OK) return rc;
     wost_batch *p = new wost_batch();
     p->dim = jobs[0].scene->dim;
+    p->device = jobs[0].scene->device;
     p->guided = guided != 0;
     p->ex = ex;
     p->jobs.assign(jobs, jobs + njobs);
@@ -450,6 +461,7 @@ extern "C" wost_status wost_batch_create(int32_t njobs, const wost_job *jobs, in
 extern "C" wost_status wost_batch_run(wost_batch *p, void *stream, wost_stats *stats) {
     if (!p) { set_error("wost_batch_run: null batch"); return WOST_ERR_INVALID_ARG; }
     if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (wost_status dc = check_device(p->device, "wost_batch_run")) return dc;
     if (!p->gexec) return WOST_OK;   // no points
     cudaStream_t st = (cudaStream_t)stream;
     WOST_CUDA(cudaEventRecord(p->ev0, st));

@@ -19,9 +19,22 @@ wost_status cuda_status(cudaError_t e, const char *what) {
     return e == cudaErrorMemoryAllocation ? WOST_ERR_OOM : WOST_ERR_CUDA;
 }
 
+wost_status check_device(int device, const char *who) {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_status(e, who);
+    if (cur != device) {
+        g_last_error = std::string(who) + ": the handle belongs to CUDA device " + std::to_string(device) +
+                       " but device " + std::to_string(cur) + " is current; make its device current first";
+        return WOST_ERR_INVALID_ARG;
+    }
+    return WOST_OK;
+}
+
 wost_status refresh_inference_copy(wost_field *f, cudaStream_t st);
 wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *loss_out_dev,
                          long long off = -1);
+wost_status train_loss_launch(wost_field *f, int dim, cudaStream_t st, float *out_dev);
 int *device_err_flag();
 wost_status device_check(cudaStream_t st);
 
@@ -59,7 +72,10 @@ wost::DevField wost_field::dev() const {
     d.log2T = desc.log2_table;
     d.nout = nout;
     d.dense_mask = dense_mask;
-    for (int l = 0; l < 16; ++l) d.res[l] = res[l];
+    for (int l = 0; l < 16; ++l) {
+        d.res[l] = res[l];
+        d.level_off[l] = (uint32_t)level_off[std::min(l, desc.levels)];
+    }
     for (int k = 0; k < 3; ++k) {
         d.lo[k] = (float)desc.lo[k];
         double e = desc.hi[k] - desc.lo[k];
@@ -86,6 +102,7 @@ extern "C" void wost_exec_defaults(wost_exec *e) {
     e->reflect = 1;
     e->c_fixed = 0.5f;
     e->train_until_wpp = 256;
+    e->rr_survival = 0.995f;
 }
 
 extern "C" void wost_field_desc_defaults(wost_field_desc *d, int32_t dim) {
@@ -154,25 +171,39 @@ extern "C" wost_status wost_create_field(const wost_field_desc *desc, wost_field
     if (!desc || !out) { set_error("wost_create_field: null argument"); return WOST_ERR_INVALID_ARG; }
     *out = nullptr;
     const wost_field_desc &d = *desc;
-    if ((d.dim != 2 && d.dim != 3) || d.K != 8 || d.levels != 16 || d.features != 2 || d.hidden != 64) {
-        set_error("wost_create_field: this build supports dim 2/3, K = 8, L = 16, F = 2, H = 64");
+    if ((d.dim != 2 && d.dim != 3) || d.K < 1 || d.K > kMaxK || d.levels != 16 || d.features != 2 || d.hidden != 64) {
+        set_error("wost_create_field: this build supports dim 2/3, K = 1..8, L = 16, F = 2, H = 64");
         return WOST_ERR_UNSUPPORTED;
     }
-    if (d.log2_table < 8 || d.log2_table > 24 || d.base_res < 2 || d.max_res < d.base_res) {
-        set_error("wost_create_field: bad table size or resolutions");
+    if (d.log2_table < 8 || d.log2_table > 24 || d.base_res < 2 || d.max_res < d.base_res ||
+        (d.grid_type != 0 && d.grid_type != 1)) {
+        set_error("wost_create_field: bad table size, resolutions or grid type");
         return WOST_ERR_INVALID_ARG;
     }
     for (int k = 0; k < d.dim; ++k)
         if (!(d.hi[k] > d.lo[k])) { set_error("wost_create_field: empty box"); return WOST_ERR_INVALID_ARG; }
+    int dev = -1;
+    WOST_CUDA(cudaGetDevice(&dev));
     auto *f = new wost_field();
     f->desc = d;
+    f->device = dev;
     f->nout = (d.dim + 2) * d.K + 1;
     f->T = (int64_t)1 << d.log2_table;
     double b = d.levels > 1 ? std::exp((std::log((double)d.max_res) - std::log((double)d.base_res)) / (d.levels - 1)) : 1.0;
+    // level l's entries start at level_off[l]: l 2^log2T in the hash grid;
+    // in the dense grid every level is dense with its own (N_l + 1)^d
+    // vertices, the levels one after the other
     for (int l = 0; l < d.levels; ++l) {
         f->res[l] = (int)std::floor(d.base_res * std::pow(b, l) + 1e-6);
         double side = f->res[l] + 1.0;
-        if (std::pow(side, d.dim) <= (double)f->T) f->dense_mask |= 1u << l;
+        const double nv = std::pow(side, d.dim);
+        if (d.grid_type == 1 || nv <= (double)f->T) f->dense_mask |= 1u << l;
+        f->level_off[l + 1] = f->level_off[l] + (d.grid_type == 1 ? (int64_t)nv : f->T);
+    }
+    if (f->level_off[d.levels] >= ((int64_t)1 << 31)) {
+        delete f;
+        set_error("wost_create_field: the dense grid needs more than 2^31 entries; lower max_res");
+        return WOST_ERR_INVALID_ARG;
     }
     const int64_t ng = f->n_grid(), nm = f->n_mlp();
     wost_status rc = WOST_OK;
@@ -202,6 +233,12 @@ extern "C" wost_status wost_create_field(const wost_field_desc *desc, wost_field
     return WOST_OK;
 }
 
+extern "C" wost_status wost_field_grid_entries(const wost_field *f, int64_t *entries) {
+    if (!f || !entries) { set_error("wost_field_grid_entries: null argument"); return WOST_ERR_INVALID_ARG; }
+    *entries = f->level_off[f->desc.levels];
+    return WOST_OK;
+}
+
 extern "C" wost_status wost_destroy_field(wost_field *f) {
     delete f;
     return WOST_OK;
@@ -210,6 +247,7 @@ extern "C" wost_status wost_destroy_field(wost_field *f) {
 extern "C" wost_status wost_field_set_params(wost_field *f, const float *grid, const float *W1, const float *W2,
                                              const float *W3, const float *b3) {
     if (!f || !grid || !W1 || !W2 || !W3 || !b3) { set_error("wost_field_set_params: null argument"); return WOST_ERR_INVALID_ARG; }
+    if (wost_status dc = check_device(f->device, "wost_field_set_params")) return dc;
     const int H = f->desc.hidden, nin = f->desc.levels * f->desc.features;
     float *d = f->mlp32;
     WOST_CUDA(cudaMemcpy(f->grid32, grid, f->n_grid() * sizeof(float), cudaMemcpyDefault));
@@ -231,6 +269,7 @@ extern "C" wost_status wost_field_set_params(wost_field *f, const float *grid, c
 extern "C" wost_status wost_field_get_params(const wost_field *f, float *grid, float *W1, float *W2, float *W3,
                                              float *b3) {
     if (!f) { set_error("wost_field_get_params: null field"); return WOST_ERR_INVALID_ARG; }
+    if (wost_status dc = check_device(f->device, "wost_field_get_params")) return dc;
     const int H = f->desc.hidden, nin = f->desc.levels * f->desc.features;
     const float *d = f->mlp32;
     WOST_CUDA(cudaDeviceSynchronize());
@@ -244,6 +283,7 @@ extern "C" wost_status wost_field_get_params(const wost_field *f, float *grid, f
 
 extern "C" wost_status wost_train_records(wost_field *f, const float *records, int64_t n, const wost_exec *exec) {
     if (!f || n < 0 || (n > 0 && !records)) { set_error("wost_train_records: invalid argument"); return WOST_ERR_INVALID_ARG; }
+    if (wost_status dc = check_device(f->device, "wost_train_records")) return dc;
     wost_exec ex;
     if (exec) ex = *exec; else wost_exec_defaults(&ex);
     wost_status rc = ensure_records(f, std::max<int64_t>(n, 1), 0);
@@ -262,6 +302,7 @@ extern "C" wost_status wost_train_records(wost_field *f, const float *records, i
 
 extern "C" wost_status wost_get_records(const wost_field *f, float *records, int64_t cap, int64_t *n) {
     if (!f || !n || cap < 0 || (cap > 0 && !records)) { set_error("wost_get_records: invalid argument"); return WOST_ERR_INVALID_ARG; }
+    if (wost_status dc = check_device(f->device, "wost_get_records")) return dc;
     *n = 0;
     if (!f->rec_ctr) return WOST_OK;
     unsigned long long c[2];
@@ -287,6 +328,7 @@ static wost_status read_loss(wost_field *f, cudaStream_t st, float *out_loss) {
 extern "C" wost_status wost_train_step(wost_scene *s, wost_field *f, const wost_exec *exec, float *out_loss) {
     if (!f) { set_error("wost_train_step: null field"); return WOST_ERR_INVALID_ARG; }
     if (s && s->dim != f->desc.dim) { set_error("wost_train_step: dimension mismatch"); return WOST_ERR_INVALID_ARG; }
+    if (wost_status dc = check_device(f->device, "wost_train_step")) return dc;
     if (!f->rec || !f->rec_ctr) { set_error("wost_train_step: no training records"); return WOST_ERR_INVALID_ARG; }
     cudaStream_t st = exec ? (cudaStream_t)exec->stream : 0;
     if (exec) f->t_samples = exec->train_samples;
@@ -296,9 +338,28 @@ extern "C" wost_status wost_train_step(wost_scene *s, wost_field *f, const wost_
     return device_check(st);
 }
 
+extern "C" wost_status wost_train_loss(wost_field *f, const wost_exec *exec, float *out_loss) {
+    if (!f || !out_loss) { set_error("wost_train_loss: invalid argument"); return WOST_ERR_INVALID_ARG; }
+    if (wost_status dc = check_device(f->device, "wost_train_loss")) return dc;
+    if (!f->rec || !f->rec_ctr) { set_error("wost_train_loss: no training records"); return WOST_ERR_INVALID_ARG; }
+    wost_exec ex;
+    if (exec) ex = *exec; else wost_exec_defaults(&ex);
+    cudaStream_t st = (cudaStream_t)ex.stream;
+    f->t_samples = ex.train_samples;
+    if (ex.out_on_device) {
+        // stays on the stream: no synchronisation
+        return train_loss_launch(f, f->desc.dim, st, out_loss);
+    }
+    wost_status rc = train_loss_launch(f, f->desc.dim, st, nullptr);
+    if (rc != WOST_OK) return rc;
+    if ((rc = read_loss(f, st, out_loss)) != WOST_OK) return rc;
+    return device_check(st);
+}
+
 extern "C" wost_status wost_train_grad(wost_field *f, const wost_exec *exec, float *out_loss, float *g_grid,
                                        float *g_W1, float *g_W2, float *g_W3, float *g_b3) {
     if (!f) { set_error("wost_train_grad: null field"); return WOST_ERR_INVALID_ARG; }
+    if (wost_status dc = check_device(f->device, "wost_train_grad")) return dc;
     if (!f->rec || !f->rec_ctr) { set_error("wost_train_grad: no training records"); return WOST_ERR_INVALID_ARG; }
     cudaStream_t st = exec ? (cudaStream_t)exec->stream : 0;
     if (exec) f->t_samples = exec->train_samples;

@@ -38,7 +38,11 @@ __host__ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t
 // 24-bit uniform in [0,1), exactly representable in float
 __host__ __device__ __forceinline__ float u01(uint32_t u) { return (float)(u >> 8) * (1.0f / 16777216.0f); }
 
-enum Purpose : uint32_t { P_MIS = 0, P_DIR = 1, P_SRC = 2, P_VMF2 = 3 };
+// purposes of the counter's last word: 3 + j are the 2D vMF retries j < 64;
+// P_NEU draws the point on the primitive chosen for <N>, P_RR the Russian
+// roulette of a long walk, and P_NKEY | id the selection key of Neumann
+// primitive id
+enum Purpose : uint32_t { P_MIS = 0, P_DIR = 1, P_SRC = 2, P_VMF2 = 3, P_NEU = 96, P_RR = 97, P_NKEY = 0x80000000u };
 
 // ---------------------------------------------------------------------------
 // analytic data functions (kind codes of wost_fn)
@@ -79,6 +83,12 @@ __device__ __forceinline__ float eval_fn(const DevFn &fn, const float *x) {
         return acc;
     }
     case 8: return coshf(fn.p[0] * x[0]) * cosf(fn.p[0] * x[1]);
+    case 9: {
+        const float X = x[0], Y = x[1], Z = D == 3 ? x[2] : 0.f;
+        return fn.p[0] + fn.p[1] * X + fn.p[2] * Y + fn.p[3] * Z + fn.p[4] * X * X + fn.p[5] * Y * Y +
+               fn.p[6] * Z * Z + fn.p[7] * X * Y + fn.p[8] * X * Z + fn.p[9] * Y * Z;
+    }
+    case 10: return fn.p[0] * atan2f(x[1], x[0]) + fn.p[1];
     }
     return __int_as_float(0x7fc00000);
 }
@@ -110,9 +120,10 @@ struct DevScene {
     float tau;            // silhouette edge-on tolerance (1e-6 * scale)
     DevBVH dir, neu, sil;
     const float4 *sil_cones;  // per silhouette-BVH node: one normal cone per child (axis.xyz, cos half-angle)
-    const float *nin_neu; // inward normal of each Neumann prim, by original id (dim floats)
-    DevFn g, f;
+    const float *nin_neu; // inward normal of each Neumann prim, by leaf slot of the Neumann BVH (dim floats)
+    DevFn g, f, h;
     int has_source;
+    int has_flux;         // nonzero Neumann flux h and Neumann primitives
 };
 
 // BVH node, normal-cone and primitive loads: generic, as the arrays may

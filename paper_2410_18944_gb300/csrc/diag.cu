@@ -53,9 +53,34 @@ __global__ void diag_umma_kernel(int a_mn, int b_mn, int N, int K, const float *
     if (tid < 32) tmem_dealloc(tm, 256);
 }
 
+// One warp waits, with the bounded wait of the walk kernels, on an mbarrier
+// that receives its single arrival only when `arrive` is set.  Without it
+// nothing ever arrives: the wait runs out after limit_ns and the kernel
+// records a timeout in the error word and returns.
+__global__ void diag_wait_kernel(unsigned long long limit_ns, int arrive, int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) { mbar_init(&bar, 1); fence_mbar_init(); }
+    __syncwarp();
+    if (arrive && threadIdx.x == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" : : "r"(smem_u32(&bar)) : "memory");
+    __syncwarp();
+    const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+    if (!ok && threadIdx.x == 0) atomicOr(err, 2);
+}
+
 }  // namespace wost
 
 using namespace wost;
+
+extern "C" wost_status wost_diag_wait(int64_t limit_ns, int32_t arrive) {
+    if (limit_ns <= 0 || limit_ns > 10000000000LL) {
+        set_error("wost_diag_wait: limit_ns must be in (0, 1e10]");
+        return WOST_ERR_INVALID_ARG;
+    }
+    diag_wait_kernel<<<1, 32>>>((unsigned long long)limit_ns, arrive ? 1 : 0, device_err_flag());
+    WOST_CUDA(cudaGetLastError());
+    return device_check(0);
+}
 
 extern "C" wost_status wost_diag_umma(int32_t a_mn, int32_t b_mn, int32_t N, int32_t K, const float *A,
                                       const float *B, float *D) {

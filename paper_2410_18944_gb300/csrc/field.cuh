@@ -32,12 +32,42 @@ constexpr int kW2Bytes = kHid * kHid * 2;        // 64 x 64
 constexpr int kW3Bytes = kOutPad * kHid * 2;     // 48 x 64
 constexpr int kWImgBytes = kW1Bytes + kW2Bytes + kW3Bytes;
 
+// The kernels read decoded outputs in one internal layout of kMaxK lobes:
+// mu'_i (kMaxK x d), kappa'_i, lambda'_i (kMaxK each), c', zero padding to
+// kOutPad.  A field of K < kMaxK lobes keeps its exchange layout (K lobes,
+// nout = (d + 2) K + 1 rows); lobes K.. of the internal layout are disabled:
+// zero weights and a lambda' bias of kOffLambda, so their mixture weight is
+// exactly zero and every gradient into them vanishes (each carries a factor
+// of the weight).  Internal row -> exchange row (-1: none) and back:
+constexpr float kOffLambda = -1.0e4f;
+__host__ __device__ inline int out_row_to_exchange(int r, int d, int K) {
+    if (r < kMaxK * d) { int i = r / d; return i < K ? i * d + r % d : -1; }
+    r -= kMaxK * d;
+    if (r < kMaxK) return r < K ? K * d + r : -1;                   // kappa'
+    r -= kMaxK;
+    if (r < kMaxK) return r < K ? K * d + K + r : -1;               // lambda'
+    return r == kMaxK ? K * (d + 2) : -1;                           // c', padding
+}
+__host__ __device__ inline int exchange_to_out_row(int e, int d, int K) {
+    if (e < K * d) return (e / d) * d + e % d;
+    e -= K * d;
+    if (e < K) return kMaxK * d + e;
+    e -= K;
+    if (e < K) return kMaxK * d + kMaxK + e;
+    return kMaxK * (d + 2);
+}
+__host__ __device__ inline bool is_off_lambda(int r, int d, int K) {
+    const int i = r - (kMaxK * d + kMaxK);
+    return i >= K && i < kMaxK;
+}
+
 struct DevField {
     int dim, K, L, log2T, nout;
     uint32_t dense_mask;          // bit l: level l indexed densely
+    uint32_t level_off[kMaxLevels];   // first entry of level l (l 2^log2T for the hash grid)
     int res[kMaxLevels];
     float lo[3], inv_ext[3];      // u = (x - lo) * inv_ext in [0,1]^d
-    const __half2 *grid16;        // L x 2^log2T entries (F = 2)
+    const __half2 *grid16;        // all levels' entries (F = 2), level l from level_off[l]
     const uint4 *wimg;            // kWImgBytes, layout above
     const float *b3;              // kOutPad (zero padded)
 };
@@ -101,7 +131,6 @@ template <int D>
 __device__ __forceinline__ void encode_row(const DevField &f, const float *x, uint8_t *xtile, int row) {
     float u[D];
     unit_coords<D>(f, x, u);
-    const size_t T = (size_t)1 << f.log2T;
 #pragma unroll kEncodeUnroll
     for (int l4 = 0; l4 < kMaxLevels; l4 += 4) {
         float feat[8];
@@ -117,9 +146,9 @@ __device__ __forceinline__ void encode_row(const DevField &f, const float *x, ui
 #if WOST_GRID_L2_ONLY
                 // the table is gathered at random: keep it out of L1 (which
                 // holds the BVH) and serve it from L2
-                __half2 hv = __ldcg(f.grid16 + (size_t)l * T + idx[m]);
+                __half2 hv = __ldcg(f.grid16 + (size_t)f.level_off[l] + idx[m]);
 #else
-                __half2 hv = __ldg(f.grid16 + (size_t)l * T + idx[m]);
+                __half2 hv = __ldg(f.grid16 + (size_t)f.level_off[l] + idx[m]);
 #endif
                 float2 g = __half22float2(hv);
                 a0 = fmaf(w[m], g.x, a0);
@@ -251,10 +280,12 @@ __device__ __forceinline__ void cta_tiles_teardown(const CtaTiles &c) {
 // host-side field state
 struct wost_field {
     wost_field_desc desc{};
+    int device = -1;                         // CUDA device the field's buffers live on
     int nout = 0;
     int64_t T = 0;
     int res[16] = {0};
     uint32_t dense_mask = 0;
+    int64_t level_off[wost::kMaxLevels + 1] = {0};   // entry offsets per level; [L] = entries of all levels
     // device buffers
     float *grid32 = nullptr, *grid_m = nullptr, *grid_v = nullptr, *grid_g = nullptr;
     __half2 *grid16 = nullptr;
@@ -280,7 +311,7 @@ struct wost_field {
         int H = desc.hidden, nin = desc.levels * desc.features;
         return (int64_t)H * nin + (int64_t)H * H + (int64_t)nout * H + nout;
     }
-    int64_t n_grid() const { return (int64_t)desc.levels * T * desc.features; }
+    int64_t n_grid() const { return level_off[desc.levels] * desc.features; }
     wost::DevField dev() const;
     ~wost_field();
 };

@@ -659,6 +659,73 @@ __device__ int ray_neumann(const DevBVH &bv, const float *o, const float *v, flo
     return best_slot;
 }
 
+// ---- Neumann boundary sample of <N> (Sec. 3.2, Eq. wost_estm) ---------------
+// Every Neumann primitive closer to x than r is a candidate with weight w its
+// length (2D) or area (3D).  The candidate with the smallest key -log(u)/w,
+// u in (0, 1] from the Philox counter (pid, wid, step, P_NKEY | id), is
+// chosen: probability w / W (W = the summed weight) whatever order the
+// traversal visits the candidates in (weighted sampling with keys,
+// Efraimidis & Spirakis 2006); ties go to the smaller id.  Returns the leaf
+// slot of the choice (-1 if there is no candidate) and W.
+template <int D>
+__device__ int neumann_pick(const DevBVH &bv, const float *x, float r, uint32_t pid, uint32_t wid, uint32_t step,
+                            uint32_t k0, uint32_t k1, float &W, int *err, Visits *vis = nullptr) {
+    constexpr int kBW = bvh_width(D);
+    W = 0.f;
+    if (bv.nprims == 0) return -1;
+    const float r2 = r * r;
+    const unsigned mask = __activemask();
+    int best_slot = -1, best_id = 0x7fffffff;
+    float best_key = __int_as_float(0x7f800000);
+    int stack[kStack];
+    float sd[kStack];
+    int sp = 0, ref = 0;
+    bool done = false;
+    float lim = r2;   // the search radius never shrinks: WOST_POP compares keys with it
+    while (__any_sync(mask, !done)) {
+        while (__any_sync(mask, !done && ref >= 0)) {
+            if (done || ref < 0) continue;
+            float k[kBW];
+            int rr[kBW];
+            bool h[kBW];
+            node_keys_d2<D>(bv.nodes, ref, x, k, rr);
+            if (vis) vis->nodes++;
+#pragma unroll
+            for (int c = 0; c < kBW; ++c) h[c] = rr[c] != kEmptyRef && k[c] < r2;
+            if (!take_children<kBW>(k, rr, h, ref, stack, sd, sp, err)) WOST_POP(stack, sd, sp, ref, done, lim);
+        }
+        if (!done && ref < 0) {
+            int s0 = leaf_start(ref), cnt = leaf_count(ref);
+            if (vis) vis->nprims += cnt;
+            for (int s = s0; s < s0 + cnt; ++s) {
+                float d2, w;
+                if (D == 2) {
+                    float4 p = ldn(bv.prims + s);
+                    float qx, qy;
+                    d2 = seg_d2<float>(p.x, p.y, p.z, p.w, x[0], x[1], qx, qy);
+                    w = sqrtf((p.z - p.x) * (p.z - p.x) + (p.w - p.y) * (p.w - p.y));
+                } else {
+                    float a[3], b[3], c[3], q[3];
+                    load_tri(bv.prims, s, a, b, c);
+                    d2 = tri_d2<float>(a, b, c, x, q);
+                    float e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+                    float n0 = e1[1] * e2[2] - e1[2] * e2[1], n1 = e1[2] * e2[0] - e1[0] * e2[2], n2 = e1[0] * e2[1] - e1[1] * e2[0];
+                    w = 0.5f * sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+                }
+                if (!(d2 < r2) || !(w > 0.f)) continue;
+                const int id = __ldg(bv.ids + s);
+                U4 u = philox(pid, wid, step, P_NKEY | (uint32_t)id, k0, k1);
+                const float uu = ((float)(u.x >> 8) + 1.f) * (1.0f / 16777216.0f);   // (0, 1]
+                const float key = -logf(uu) / w;
+                W += w;
+                if (key < best_key || (key == best_key && id < best_id)) { best_key = key; best_slot = s; best_id = id; }
+            }
+            WOST_POP(stack, sd, sp, ref, done, lim);
+        }
+    }
+    return best_slot;
+}
+
 // number of crossings of the ray o + t v (t > 0) with all primitives of a BVH
 template <int D>
 __device__ int ray_count(const DevBVH &bv, const float *o, const float *v, int *err) {

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kGuidedBlock, 1) decode_kernel(DevField f, con
         float raw[kOutPad];
         if (!mlp_tile_forward(t, f, row, row == 0, raw, err)) break;
         if (i < n)
-            for (int k = 0; k < nout; ++k) out[i * nout + k] = raw[k];
+            for (int k = 0; k < nout; ++k) out[i * nout + k] = raw[exchange_to_out_row(k, D, f.K)];
     }
     cta_tiles_teardown(ct);
 }
@@ -176,6 +176,7 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
     g.o.c_fixed = ex.c_fixed;
     g.o.reflect = ex.reflect;
     g.o.flush_polls = kFlushPolls;
+    g.o.wait_ns = ex.wait_ns > 0 ? (unsigned long long)ex.wait_ns : kWaitNs;
     g.o.err = a.err;
     g.o.stat = a.stat;
     f->t_c_mode = ex.c_mode;
@@ -295,6 +296,7 @@ using namespace wost;
 extern "C" wost_status wost_field_decode(wost_field *f, const double *points, int64_t n, float *out_raw,
                                          const wost_exec *exec) {
     if (!f || n < 0 || (n > 0 && (!points || !out_raw))) { set_error("wost_field_decode: invalid argument"); return WOST_ERR_INVALID_ARG; }
+    if (wost_status dc = check_device(f->device, "wost_field_decode")) return dc;
     if (n == 0) return WOST_OK;
     wost_exec ex;
     if (exec) ex = *exec; else wost_exec_defaults(&ex);

@@ -120,6 +120,7 @@ struct WsOpts {
     float *scratch;              // [slot][scratch_steps][kRecFloats]
     int scratch_steps;
     uint32_t flush_polls;        // server polls before closing a partial tile
+    unsigned long long wait_ns;  // limit of the waits on other warps (tile filled, decoded, consumed)
     int *err;
     unsigned long long *stat;
 };
@@ -129,19 +130,19 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 }
 
 // all lanes of the calling warp poll (converged); returns false on give-up
-__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity) {
-    return mbar_wait_bounded(bar, parity);
+__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, unsigned long long limit_ns) {
+    return mbar_wait_bounded(bar, parity, limit_ns);
 }
 
 // until *count reaches target (monotonic); false on give-up
-__device__ __forceinline__ bool wait_consumed(const unsigned *count, unsigned target) {
+__device__ __forceinline__ bool wait_consumed(const unsigned *count, unsigned target, unsigned long long limit_ns) {
     if (*(volatile const unsigned *)count >= target) {
         __threadfence_block();
         return true;
     }
     const unsigned long long t0 = globaltimer_ns();
     while (*(volatile const unsigned *)count < target) {
-        if (globaltimer_ns() - t0 > kWaitNs) return false;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
         __nanosleep(64);
     }
     __threadfence_block();
@@ -231,7 +232,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
                 const unsigned long long t0 = globaltimer_ns();
                 for (;;) {
                     if (mbar_try_wait(&ctl->full[b], k & 1u)) { go = 1; break; }
-                    if (globaltimer_ns() - t0 > kWaitNs) break;
+                    if (globaltimer_ns() - t0 > o.wait_ns) break;
                     int q = *(volatile int *)&ctl->qclaim;
                     const int alive = *(volatile int *)&ctl->alive;
                     // every walker warp still running has claimed a quarter of
@@ -414,7 +415,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
             qi = __shfl_sync(0xffffffffu, qi, 0);
             const int T = qi >> 2, quarter = qi & 3, b = T % kNT;
             const uint32_t k = (uint32_t)(T / kNT);
-            if (T >= kNT && !wait_consumed(&ctl->consumed[b], 4u * k)) { failed = true; break; }
+            if (T >= kNT && !wait_consumed(&ctl->consumed[b], 4u * k, o.wait_ns)) { failed = true; break; }
             const int row = 32 * quarter + lane;
             if (enc) encode_row<D>(src.field(w), w.x, Xb(b), row);
             else zero_row(Xb(b), row, kFeat);
@@ -427,7 +428,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
             // on the barrier while the others' geometry runs
             __syncwarp();
             const bool live = active;
-            if (!ws_wait(&ctl->done[b][quarter], k & 1u)) { failed = true; break; }
+            if (!ws_wait(&ctl->done[b][quarter], k & 1u, o.wait_ns)) { failed = true; break; }
             float nu[D];
             bool zero_density = false;
             float wgt = 1.f, ptil = 0.f;
@@ -476,7 +477,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
                         float n2 = onN && D == 3 ? w.n[D - 1] : 0.f;
                         rr[0] = make_float4(w.x[0], w.x[1], D == 3 ? w.x[2] : 0.f, nu[0]);
                         rr[1] = make_float4(nu[1], D == 3 ? nu[2] : 0.f, onN ? w.n[0] : 0.f, onN ? w.n[1] : 0.f);
-                        rr[2] = make_float4(n2, ptil, wgt, S);
+                        rr[2] = make_float4(n2, ptil, wgt * roulette_scale(src.env(w), w.k), S);
                     }
                     w.T *= wgt;
                     step_move<D>(w, src.env(w), nu, r, &vis);

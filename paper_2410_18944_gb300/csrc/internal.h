@@ -34,6 +34,7 @@ struct FieldDev;  // defined in field.cuh
 
 struct wost_scene {
     int dim = 0;
+    int device = -1;              // CUDA device the scene's data lives on (current at creation)
     int64_t nverts = 0, nprims = 0;
     uint32_t scene_id = 0;
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -81,4 +82,9 @@ int num_sms();
 double walk_alg_bytes(int D, bool guided, const unsigned long long *hs, int64_t records);
 int *device_err_flag();                  // device word: bit 0 stack overflow, bit 1 wait timeout
 wost_status device_check(cudaStream_t st);
+// WOST_OK if `device` (a scene's or field's) is the current CUDA device; else
+// WOST_ERR_INVALID_ARG (or the CUDA error of the lookup) with a message naming
+// `who`.  Called before any launch: a kernel on the wrong device would read
+// another GPU's pointers.
+wost_status check_device(int device, const char *who);
 }

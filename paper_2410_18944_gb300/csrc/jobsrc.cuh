@@ -56,7 +56,7 @@ struct SoloSrc {
         return a.status[w.pid] == 0;
     }
     __device__ __forceinline__ StepEnv env(const Walk<D> &) const {
-        return StepEnv{*sc, a.eps, a.eps64, a.maxsteps, a.key0, a.key1, a.err};
+        return StepEnv{*sc, a.eps, a.eps64, a.maxsteps, a.key0, a.key1, a.err, a.rr_depth, a.rr_q};
     }
     __device__ __forceinline__ void finish(const Walk<D> &w) const { finish_walk(a, w.pid, w.acc); }
     __device__ __forceinline__ const DevField &field(const Walk<D> &) const { return *f; }
@@ -148,6 +148,8 @@ struct DevJob {
     float eps;
     double eps64;
     uint32_t key0, key1;
+    int rr_depth;                // Russian roulette from this step on (0 = off)
+    float rr_q;                  // its survival probability
     RecDest rd;                  // the field's record buffer
     double *out_mean, *out_var;  // npoints each (device; out_var nullable)
 };
@@ -208,7 +210,7 @@ struct BatchSrc {
     }
     __device__ __forceinline__ StepEnv env(const Walk<D> &w) const {
         const DevJob &J = b.jobs[w.job];
-        return StepEnv{J.sc, J.eps, J.eps64, J.maxsteps, J.key0, J.key1, b.err};
+        return StepEnv{J.sc, J.eps, J.eps64, J.maxsteps, J.key0, J.key1, b.err, J.rr_depth, J.rr_q};
     }
     __device__ __forceinline__ void finish(const Walk<D> &w) const {
         const size_t i = (size_t)b.jobs[w.job].point_off + w.pid;

@@ -217,6 +217,15 @@ __device__ __forceinline__ int lane_after_query(Walk<D> &w, LaneQuery<D> &Q, Lan
             Q.q = kQNone;
             return kLaneEnded;
         }
+        if (roulette_on(env, w.k)) {
+            if (!roulette_survives(env, w.pid, w.wid, w.k)) {
+                gv = 0.f;
+                trunc = false;
+                Q.q = kQNone;
+                return kLaneEnded;
+            }
+            w.T *= 1.f / env.rr_q;
+        }
         query_begin<D>(Q, sc, kQSil, L.RD * L.RD);
         return kLaneGo;
     }
@@ -224,7 +233,13 @@ __device__ __forceinline__ int lane_after_query(Walk<D> &w, LaneQuery<D> &Q, Lan
         const float R = fminf(sqrtf(Q.best), L.RD);
         L.r = fmaxf(R, env.eps);
         L.S = 0.f;
-        if (!sc.has_source) return kLaneDirection;
+        if (!sc.has_source) {
+            if (sc.has_flux) {
+                L.S = -neumann_term<D>(w, sc, L.r, env.key0, env.key1, env.err, nullptr);
+                w.acc += w.T * L.S;
+            }
+            return kLaneDirection;
+        }
         U4 u = philox(w.pid, w.wid, (uint32_t)w.k, P_SRC, env.key0, env.key1);
         float vs[D];
         uniform_dir<D>(u01(u.x), u01(u.y), vs);
@@ -247,6 +262,7 @@ __device__ __forceinline__ int lane_after_query(Walk<D> &w, LaneQuery<D> &Q, Lan
             for (int i = 0; i < D; ++i) y[i] = w.x[i] + L.rho * Q.v[i];
             L.S = -(L.r * L.r / (2.f * D)) * eval_fn<D>(sc.f, y);
         }
+        if (sc.has_flux) L.S -= neumann_term<D>(w, sc, L.r, env.key0, env.key1, env.err, nullptr);
         w.acc += w.T * L.S;
         return kLaneDirection;
     }

@@ -114,6 +114,9 @@ extern "C" wost_status wost_solve_plain_static(wost_scene *s, const double *poin
                   "use wost_solve or split the points");
         return WOST_ERR_INVALID_ARG;
     }
+    // the scene's BVHs must be on the current device: the array looked up
+    // below, and the kernels, are the current device's
+    if (wost_status dc = check_device(s->device, "wost_solve_plain_static")) return dc;
     unsigned char *base = nullptr;
     wost_status rc = static_base(&base);
     if (rc != WOST_OK) return rc;

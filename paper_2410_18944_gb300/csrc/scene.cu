@@ -313,7 +313,7 @@ wost_status upload(wost_scene *s, const std::vector<T> &v, const T **out) {
 }
 
 bool valid_fn(const wost_fn &f) {
-    if (f.kind < 0 || f.kind > 8) return false;
+    if (f.kind < 0 || f.kind > 10) return false;
     if (f.kind == 7 && (f.params[0] < 0 || f.params[0] > 8)) return false;
     return true;
 }
@@ -356,7 +356,6 @@ extern "C" wost_status wost_create_scene(const wost_scene_desc *desc, wost_scene
         set_error("wost_create_scene: unknown data-function kind");
         return WOST_ERR_INVALID_ARG;
     }
-    if (desc->h.kind != 0) { set_error("wost_create_scene: nonzero Neumann flux is not supported"); return WOST_ERR_UNSUPPORTED; }
     const int64_t nv = desc->nverts, np = desc->nprims;
     int ndir = 0;
     for (int64_t i = 0; i < np; ++i) {
@@ -370,9 +369,12 @@ extern "C" wost_status wost_create_scene(const wost_scene_desc *desc, wost_scene
     for (int64_t i = 0; i < nv * d; ++i)
         if (!std::isfinite(desc->verts[i])) { set_error("wost_create_scene: non-finite vertex"); return WOST_ERR_INVALID_ARG; }
     if (ndir == 0) { set_error("wost_create_scene: no Dirichlet primitive (ill-posed)"); return WOST_ERR_ILL_POSED; }
+    int dev = -1;
+    WOST_CUDA(cudaGetDevice(&dev));
 
     auto *s = new wost_scene();
     s->dim = d;
+    s->device = dev;
     s->nverts = nv;
     s->nprims = np;
     s->scene_id = desc->scene_id;
@@ -561,12 +563,26 @@ extern "C" wost_status wost_create_scene(const wost_scene_desc *desc, wost_scene
     s->dev.g = to_dev(desc->g);
     s->dev.f = to_dev(desc->f);
     s->dev.has_source = desc->f.kind != 0;
+    s->dev.h = to_dev(desc->h);
+    s->dev.has_flux = desc->h.kind != 0 && s->nneu > 0;
     *out = s;
     return WOST_OK;
 }
 
 extern "C" wost_status wost_destroy_scene(wost_scene *s) {
     delete s;
+    return WOST_OK;
+}
+
+extern "C" wost_status wost_scene_device(const wost_scene *s, int32_t *device) {
+    if (!s || !device) { set_error("wost_scene_device: null argument"); return WOST_ERR_INVALID_ARG; }
+    *device = s->device;
+    return WOST_OK;
+}
+
+extern "C" wost_status wost_diag_scene_rebind(wost_scene *s, int32_t device) {
+    if (!s) { set_error("wost_diag_scene_rebind: null scene"); return WOST_ERR_INVALID_ARG; }
+    s->device = device;
     return WOST_OK;
 }
 

@@ -50,6 +50,7 @@ struct TrainArgs {
     long long off_fixed;                    // stratum of this step (< 0: from the Adam step count)
     const unsigned long long *step;         // Adam step count before this step
     unsigned long long *used;               // records this step used
+    int loss_only;                          // forward recomputation and loss only, no gradients
     int *err;
 };
 
@@ -196,7 +197,6 @@ __global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
     if (blockIdx.x == 0 && tid == 0) *a.used = (unsigned long long)nrec;
     const float inv_n = nrec > 0 ? 1.f / (float)nrec : 0.f;
     const long long ntiles = (nrec + 127) / 128;
-    const size_t T = (size_t)1 << a.f.log2T;
     bool have_acc = false, ok = true;
     float db3 = 0.f;      // column `row` (< kOutPad) of the bias gradient
     double loss_local = 0.0;
@@ -243,6 +243,7 @@ __global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
         float dy[kOutPad];
         if (valid) loss_local += record_grad<D>(a, rec, raw, inv_n, dy);
         else for (int i = 0; i < kOutPad; ++i) dy[i] = 0.f;
+        if (a.loss_only) continue;   // uniform over the tile: no backward pass
         for (int c = 0; c < kOutPad; c += 8) st_row8_split(t.G, t.Gl, row, c, 128, dy + c);
         {
             float z8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
                     float w[1 << D];
                     level_corners<D>(a.f, l, u, idx, w);
                     for (int m = 0; m < (1 << D); ++m) {
-                        float *gp = a.g_grid + ((size_t)l * T + idx[m]) * 2;
+                        float *gp = a.g_grid + ((size_t)a.f.level_off[l] + idx[m]) * 2;
                         atomicAdd(reinterpret_cast<float2 *>(gp), make_float2(w[m] * dx[2 * l], w[m] * dx[2 * l + 1]));
                     }
                 }
@@ -328,12 +329,14 @@ __global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
         // TMEM loads are warp-collective: every lane loads, then stores conditionally
         float v[kHid];
         ld_cols(t.acc3, row, kHid, v);
-        if (row < kOutPad) for (int i = 0; i < kHid; ++i) atomicAdd(a.g_W3 + (size_t)row * kHid + i, v[i]);
+        // internal output row -> exchange row (padding and disabled lobes: none)
+        const int er = row < kOutPad ? out_row_to_exchange(row, a.f.dim, a.f.K) : -1;
+        if (er >= 0) for (int i = 0; i < kHid; ++i) atomicAdd(a.g_W3 + (size_t)er * kHid + i, v[i]);
         ld_cols(t.acc2, row, kHid, v);
         if (row >= 64) for (int i = 0; i < kHid; ++i) atomicAdd(a.g_W2 + (size_t)(row - 64) * kHid + i, v[i]);
         ld_cols(t.acc1, row, kFeat, v);
         if (row < 64) for (int i = 0; i < kFeat; ++i) atomicAdd(a.g_W1 + (size_t)row * kFeat + i, v[i]);
-        if (row < kOutPad) atomicAdd(a.g_b3 + row, db3);
+        if (er >= 0) atomicAdd(a.g_b3 + er, db3);
     }
     // loss: warp reduction then one atomic per warp
     for (int o = 16; o; o >>= 1) loss_local += __shfl_xor_sync(0xffffffffu, loss_local, o);
@@ -380,7 +383,7 @@ __global__ void grid_to_half_kernel(const float *g32, __half2 *g16, int64_t n) {
 }
 
 // FP32 MLP master (exchange layout) -> BF16 core-matrix weight image + padded bias
-__global__ void weight_image_kernel(const float *mlp, int nout, uint8_t *img, float *b3pad) {
+__global__ void weight_image_kernel(const float *mlp, int nout, int dim, int K, uint8_t *img, float *b3pad) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float *W1 = mlp, *W2 = W1 + kHid * kFeat, *W3 = W2 + kHid * kHid, *b3 = W3 + nout * kHid;
     __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(img);
@@ -394,16 +397,21 @@ __global__ void weight_image_kernel(const float *mlp, int nout, uint8_t *img, fl
     }
     if (i < kOutPad * kHid) {
         int r = i / kHid, c = i % kHid;
-        float val = r < nout ? W3[r * kHid + c] : 0.f;
+        const int er = out_row_to_exchange(r, dim, K);
+        float val = er >= 0 ? W3[er * kHid + c] : 0.f;
         o[(kW1Bytes + kW2Bytes + cm_offset(r, c, kHid)) / 2] = __float2bfloat16_rn(val);
     }
-    if (i < kOutPad) b3pad[i] = i < nout ? b3[i] : 0.f;
+    if (i < kOutPad) {
+        const int er = out_row_to_exchange(i, dim, K);
+        b3pad[i] = er >= 0 ? b3[er] : (is_off_lambda(i, dim, K) ? kOffLambda : 0.f);
+    }
 }
 
 wost_status refresh_inference_copy(wost_field *f, cudaStream_t st) {
-    int64_t ne = (int64_t)f->desc.levels * f->T;
+    const int64_t ne = f->level_off[f->desc.levels];   // lattice entries of all levels (either encoding)
     grid_to_half_kernel<<<(int)((ne + 255) / 256), 256, 0, st>>>(f->grid32, f->grid16, ne);
-    weight_image_kernel<<<(kHid * kHid + 255) / 256, 256, 0, st>>>(f->mlp32, f->nout, f->wimg, f->b3pad);
+    weight_image_kernel<<<(kHid * kHid + 255) / 256, 256, 0, st>>>(f->mlp32, f->nout, f->desc.dim, f->desc.K,
+                                                                    f->wimg, f->b3pad);
     WOST_CUDA(cudaGetLastError());
     return WOST_OK;
 }
@@ -422,9 +430,12 @@ wost_status train_prepare(int dim) {
 }
 
 // gradient of the mean loss over the record buffer into f->grid_g / f->mlp_g
-wost_status train_grad_launch(wost_field *f, int dim, cudaStream_t st, long long off) {
-    WOST_CUDA(cudaMemsetAsync(f->grid_g, 0, f->n_grid() * sizeof(float), st));
-    WOST_CUDA(cudaMemsetAsync(f->mlp_g, 0, f->n_mlp() * sizeof(float), st));
+// (loss_only: the loss alone, the gradient buffers untouched)
+wost_status train_grad_launch(wost_field *f, int dim, cudaStream_t st, long long off, bool loss_only = false) {
+    if (!loss_only) {
+        WOST_CUDA(cudaMemsetAsync(f->grid_g, 0, f->n_grid() * sizeof(float), st));
+        WOST_CUDA(cudaMemsetAsync(f->mlp_g, 0, f->n_mlp() * sizeof(float), st));
+    }
     WOST_CUDA(cudaMemsetAsync(f->loss_acc, 0, sizeof(double), st));
     TrainArgs a{};
     a.f = f->dev();
@@ -445,12 +456,27 @@ wost_status train_grad_launch(wost_field *f, int dim, cudaStream_t st, long long
     a.off_fixed = off;
     a.step = f->adam_step();
     a.used = f->used_records();
+    a.loss_only = loss_only ? 1 : 0;
     a.err = device_err_flag();
     // one CTA per SM: each CTA holds all 512 TMEM columns of its SM
     wost_status rc = train_prepare(dim);
     if (rc != WOST_OK) return rc;
     if (dim == 2) train_kernel<2><<<num_sms(), kTrainBlock, kTrainSmem, st>>>(a);
     else train_kernel<3><<<num_sms(), kTrainBlock, kTrainSmem, st>>>(a);
+    WOST_CUDA(cudaGetLastError());
+    return WOST_OK;
+}
+
+__global__ void loss_out_kernel(const double *acc, float *out) {
+    unsigned long long n = reinterpret_cast<const unsigned long long *>(acc)[2];
+    *out = n > 0 ? (float)(acc[0] / (double)n) : 0.f;
+}
+
+// mean loss of the step's records, written to a device float on the stream
+wost_status train_loss_launch(wost_field *f, int dim, cudaStream_t st, float *out_dev) {
+    wost_status rc = train_grad_launch(f, dim, st, -1, true);
+    if (rc != WOST_OK) return rc;
+    if (out_dev) loss_out_kernel<<<1, 1, 0, st>>>(reinterpret_cast<const double *>(f->loss_acc), out_dev);
     WOST_CUDA(cudaGetLastError());
     return WOST_OK;
 }

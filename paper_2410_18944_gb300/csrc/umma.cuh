@@ -136,13 +136,17 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-// bounded wait: false once kWaitNs have passed (the caller reports a timeout)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// bounded wait: false once limit_ns have passed (the caller reports a
+// timeout).  Waits for the completion of the CTA's own tensor-core work keep
+// the default: that work always completes, and the CTA must not release its
+// TMEM while an MMA may still write it.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > kWaitNs) return false;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
 

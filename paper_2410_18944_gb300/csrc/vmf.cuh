@@ -170,13 +170,18 @@ __device__ __forceinline__ bool sample_direction(const Mixture<D> &m, float c, u
                                                  uint32_t step, uint32_t k0, uint32_t k1, float *nu) {
     U4 u = philox(pid, wid, step, P_MIS, k0, k1);
     if (u01(u.x) < c) {
-        // first lobe whose running CDF exceeds u1
+        // first lobe whose running CDF exceeds u1 (past the end, which
+        // rounding allows: the last lobe of nonzero weight)
         float u1 = u01(u.y), cdf = 0.f;
-        int lobe = K - 1;
+        int lobe = -1;
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             cdf += m.lam[i];
             if (u1 < cdf) { lobe = i; break; }
+        }
+        if (lobe < 0) {
+            lobe = K - 1;
+            while (lobe > 0 && !(m.lam[lobe] > 0.f)) --lobe;
         }
         const float *mu = m.mu + lobe * D;
         if (D == 2) {
@@ -266,12 +271,17 @@ __device__ __forceinline__ bool sample_direction_row(const RowMixture<D, K> &m, 
                                                      uint32_t step, uint32_t k0, uint32_t k1, float *nu) {
     U4 u = philox(pid, wid, step, P_MIS, k0, k1);
     if (u01(u.x) < c) {
-        // first lobe whose running CDF exceeds u1
+        // first lobe whose running CDF exceeds u1 (past the end, which
+        // rounding allows: the last lobe of nonzero weight)
         float u1 = u01(u.y), cdf = 0.f;
-        int lobe = K - 1;
+        int lobe = -1;
         for (int i = 0; i < K; ++i) {
             cdf += m.lam[i];
             if (u1 < cdf) { lobe = i; break; }
+        }
+        if (lobe < 0) {
+            lobe = K - 1;
+            while (lobe > 0 && !(m.lam[lobe] > 0.f)) --lobe;
         }
         float mu[D];
         m.mu(lobe, mu);

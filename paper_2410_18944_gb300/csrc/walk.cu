@@ -116,7 +116,11 @@ __global__ void q_sil_kernel(DevScene sc, const int64_t *keys, const double *p, 
     od[i] = s >= 0 ? sqrtf(b) : b;
 }
 
-template <int D>
+// kExit = false: first hit of any orientation, FP64 re-test of the winner
+// against tmax.  kExit = true: the cast of a walk step (step_move): exit
+// crossings only, from t > -tneg, and the winner re-tested in FP64 against
+// the FP32 tmax when its FP32 parameter lies within the rounding band below it.
+template <int D, bool kExit>
 __global__ void q_ray_kernel(DevScene sc, const double *o, const double *v, const double *tmax,
                              const int32_t *skip_id, const int *slot_of_id, int64_t n, int32_t *oid, float *ot,
                              int *err) {
@@ -127,10 +131,20 @@ __global__ void q_ray_kernel(DevScene sc, const double *o, const double *v, cons
     int skip = skip_id && skip_id[i] >= 0 ? slot_of_id[skip_id[i]] : -1;
     float t;
     float tm = (float)tmax[i];
-    int s = ray_neumann<D>(sc.neu, x, d, tm, skip, t, err);
-    if (s >= 0) {
-        double t64;
-        if (!ray_prim64<D>(sc.neu, s, x, d, t64) || t64 > tmax[i]) s = -1;
+    int s;
+    if (kExit) {
+        const float tneg = kRoundBand * sc.scale;
+        s = ray_neumann<D, true>(sc.neu, x, d, tm, skip, t, err, nullptr, tneg);
+        if (s >= 0 && tm - t <= kRoundBand * (sc.scale + tm)) {
+            double t64;
+            if (!ray_prim64<D, true>(sc.neu, s, x, d, t64, tneg) || t64 > (double)tm) s = -1;
+        }
+    } else {
+        s = ray_neumann<D>(sc.neu, x, d, tm, skip, t, err);
+        if (s >= 0) {
+            double t64;
+            if (!ray_prim64<D>(sc.neu, s, x, d, t64) || t64 > tmax[i]) s = -1;
+        }
     }
     oid[i] = s >= 0 ? sc.neu.ids[s] : -1;
     ot[i] = s >= 0 ? t : __int_as_float(0x7f800000);
@@ -206,6 +220,15 @@ extern "C" wost_status wost_solve(wost_scene *s, wost_field *field, const double
     }
     if (npoints > 0 && !points) { set_error("wost_solve: null points"); return WOST_ERR_INVALID_ARG; }
     if (guided && !field) { set_error("wost_solve: guided solve needs a field"); return WOST_ERR_INVALID_ARG; }
+    if (exec && (exec->rr_depth < 0 || (exec->rr_depth > 0 && !(exec->rr_survival > 0.f && exec->rr_survival <= 1.f)))) {
+        set_error("wost_solve: rr_depth must be >= 0 and rr_survival in (0, 1]");
+        return WOST_ERR_INVALID_ARG;
+    }
+    {
+        wost_status dc = check_device(s->device, "wost_solve (scene)");
+        if (dc == WOST_OK && guided) dc = check_device(field->device, "wost_solve (field)");
+        if (dc != WOST_OK) return dc;
+    }
     wost_exec ex;
     if (exec) ex = *exec; else wost_exec_defaults(&ex);
     if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -247,6 +270,8 @@ extern "C" wost_status wost_solve(wost_scene *s, wost_field *field, const double
     a.key1 = (uint32_t)(ex.seed >> 32) + s->scene_id;
     a.stat = ctr + 8;
     a.err = err_flag();
+    a.rr_depth = ex.rr_depth;
+    a.rr_q = ex.rr_survival;
 
     if (D == 2) classify_kernel<2><<<blocks_for(npoints, 128), 128, 0, st>>>(a, shell_val);
     else classify_kernel<3><<<blocks_for(npoints, 128), 128, 0, st>>>(a, shell_val);
@@ -313,6 +338,7 @@ extern "C" wost_status wost_solve(wost_scene *s, wost_field *field, const double
 extern "C" wost_status wost_query_closest(wost_scene *s, const double *points, int64_t n, int32_t *out_prim,
                                           float *out_dist) {
     if (!s || (n > 0 && (!points || !out_prim || !out_dist)) || n < 0) { set_error("wost_query_closest: invalid argument"); return WOST_ERR_INVALID_ARG; }
+    if (wost_status dc = check_device(s->device, "wost_query_closest")) return dc;
     if (n == 0) return WOST_OK;
     Staged<double> p;
     wost_status rc;
@@ -335,6 +361,7 @@ extern "C" wost_status wost_query_closest(wost_scene *s, const double *points, i
 extern "C" wost_status wost_query_silhouette(wost_scene *s, const double *points, int64_t n, int64_t *out_elem,
                                              float *out_dist) {
     if (!s || (n > 0 && (!points || !out_elem || !out_dist)) || n < 0) { set_error("wost_query_silhouette: invalid argument"); return WOST_ERR_INVALID_ARG; }
+    if (wost_status dc = check_device(s->device, "wost_query_silhouette")) return dc;
     if (n == 0) return WOST_OK;
     Staged<double> p;
     wost_status rc;
@@ -354,13 +381,18 @@ extern "C" wost_status wost_query_silhouette(wost_scene *s, const double *points
     return check_err_flag(0);
 }
 
-extern "C" wost_status wost_query_ray(wost_scene *s, const double *org, const double *dir, const double *tmax,
-                                      const int32_t *skip, int64_t n, int32_t *out_prim, float *out_t) {
-    if (!s || n < 0 || (n > 0 && (!org || !dir || !tmax || !out_prim || !out_t))) { set_error("wost_query_ray: invalid argument"); return WOST_ERR_INVALID_ARG; }
+namespace {
+wost_status query_ray(bool exit_only, const char *who, wost_scene *s, const double *org, const double *dir,
+                      const double *tmax, const int32_t *skip, int64_t n, int32_t *out_prim, float *out_t) {
+    if (!s || n < 0 || (n > 0 && (!org || !dir || !tmax || !out_prim || !out_t))) {
+        set_error(std::string(who) + ": invalid argument");
+        return WOST_ERR_INVALID_ARG;
+    }
+    if (wost_status dc = check_device(s->device, who)) return dc;
     if (n == 0) return WOST_OK;
     if (skip)
         for (int64_t i = 0; i < n; ++i)
-            if (skip[i] >= s->nprims) { set_error("wost_query_ray: skip id out of range"); return WOST_ERR_INVALID_ARG; }
+            if (skip[i] >= s->nprims) { set_error(std::string(who) + ": skip id out of range"); return WOST_ERR_INVALID_ARG; }
     Staged<double> po, pv, pt;
     Staged<int32_t> ps;
     wost_status rc;
@@ -376,14 +408,28 @@ extern "C" wost_status wost_query_ray(wost_scene *s, const double *org, const do
     float *dt;
     WOST_CUDA(cudaMalloc(&di, n * sizeof(int32_t)));
     WOST_CUDA(cudaMalloc(&dt, n * sizeof(float)));
-    if (s->dim == 2) q_ray_kernel<2><<<blocks_for(n, 128), 128>>>(s->dev, po.dev, pv.dev, pt.dev, ps.dev, slot_of, n, di, dt, err_flag());
-    else q_ray_kernel<3><<<blocks_for(n, 128), 128>>>(s->dev, po.dev, pv.dev, pt.dev, ps.dev, slot_of, n, di, dt, err_flag());
+    const int nb = blocks_for(n, 128);
+    if (s->dim == 2 && exit_only) q_ray_kernel<2, true><<<nb, 128>>>(s->dev, po.dev, pv.dev, pt.dev, ps.dev, slot_of, n, di, dt, err_flag());
+    else if (s->dim == 2) q_ray_kernel<2, false><<<nb, 128>>>(s->dev, po.dev, pv.dev, pt.dev, ps.dev, slot_of, n, di, dt, err_flag());
+    else if (exit_only) q_ray_kernel<3, true><<<nb, 128>>>(s->dev, po.dev, pv.dev, pt.dev, ps.dev, slot_of, n, di, dt, err_flag());
+    else q_ray_kernel<3, false><<<nb, 128>>>(s->dev, po.dev, pv.dev, pt.dev, ps.dev, slot_of, n, di, dt, err_flag());
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpy(out_prim, di, n * sizeof(int32_t), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(out_t, dt, n * sizeof(float), cudaMemcpyDeviceToHost);
     cudaFree(di);
     cudaFree(dt);
     cudaFree(slot_of);
-    if (e != cudaSuccess) return cuda_status(e, "wost_query_ray");
+    if (e != cudaSuccess) return cuda_status(e, who);
     return check_err_flag(0);
+}
+}  // namespace
+
+extern "C" wost_status wost_query_ray(wost_scene *s, const double *org, const double *dir, const double *tmax,
+                                      const int32_t *skip, int64_t n, int32_t *out_prim, float *out_t) {
+    return query_ray(false, "wost_query_ray", s, org, dir, tmax, skip, n, out_prim, out_t);
+}
+
+extern "C" wost_status wost_query_ray_exit(wost_scene *s, const double *org, const double *dir, const double *tmax,
+                                           const int32_t *skip, int64_t n, int32_t *out_prim, float *out_t) {
+    return query_ray(true, "wost_query_ray_exit", s, org, dir, tmax, skip, n, out_prim, out_t);
 }

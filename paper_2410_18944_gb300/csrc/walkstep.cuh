@@ -3,7 +3,10 @@
 //   1. closest Dirichlet point; stop inside the epsilon-shell (FP64 re-test)
 //      or at the step cap, adding T g(xbar) to the point's FP64 sums;
 //   2. star radius r = max(min(R_D, R_S), eps) from the closest silhouette;
-//   3. source term -(r^2 / 2d) f(y), y ~ Green-function density, if visible;
+//   0. Russian roulette from step rr_depth on (after the epsilon-shell test):
+//      go on with probability q (throughput / q), else end with value 0;
+//   3. source term -(r^2 / 2d) f(y), y ~ Green-function density, if visible,
+//      and the Neumann term -<N> when the flux is nonzero;
 //   4. (caller) direction nu and step weight;
 //   5. first Neumann hit within r (FP64 re-test of the winner) or x + r nu.
 // Random numbers: Philox4x32-10, counter (point, walk, step, purpose).
@@ -32,6 +35,8 @@ struct WalkArgs {
     uint32_t key0, key1;
     unsigned long long *stat;  // [0] walk-steps, [1] truncated, [2] walks, [3..6] node/Dirichlet/silhouette/Neumann visits
     int *err;
+    int rr_depth;              // Russian roulette from this step on (0 = off)
+    float rr_q;                // survival probability of a roulette step
 };
 
 // what one step needs besides the walk state: the walk's scene and the
@@ -43,10 +48,26 @@ struct StepEnv {
     int maxsteps;
     uint32_t key0, key1;
     int *err;
+    int rr_depth;
+    float rr_q;
 };
 
 __device__ __forceinline__ StepEnv env_of(const WalkArgs &a) {
-    return StepEnv{a.sc, a.eps, a.eps64, a.maxsteps, a.key0, a.key1, a.err};
+    return StepEnv{a.sc, a.eps, a.eps64, a.maxsteps, a.key0, a.key1, a.err, a.rr_depth, a.rr_q};
+}
+
+// Russian roulette (Sec. 6.1 enables it beyond 128 steps; the survival rule
+// is a reading: a fixed probability q).  A step k >= rr_depth that survives
+// divides the throughput by q, and for the suffix pass its weight and
+// non-recursive terms carry the same 1 / q: roulette_scale(k).
+__device__ __forceinline__ bool roulette_on(const StepEnv &a, int k) { return a.rr_depth > 0 && k >= a.rr_depth; }
+__device__ __forceinline__ float roulette_scale(const StepEnv &a, int k) {
+    return roulette_on(a, k) ? 1.f / a.rr_q : 1.f;
+}
+// the step's roulette draw (counter purpose P_RR): true if the walk goes on
+__device__ __forceinline__ bool roulette_survives(const StepEnv &a, uint32_t pid, uint32_t wid, int k) {
+    U4 u = philox(pid, wid, (uint32_t)k, P_RR, a.key0, a.key1);
+    return u01(u.x) < a.rr_q;
 }
 
 template <int D>
@@ -111,8 +132,51 @@ __device__ __forceinline__ void finish_walk(const WalkArgs &a, uint32_t pid, flo
     atomicAdd(a.sum2 + pid, (double)value * (double)value);
 }
 
-// Steps 1-3.  Returns true if the walk ended (its value already added).
-// On return false: r (star radius) and S (this step's source term).
+// Neumann contribution <N> of a step (Sec. 3.2, Eq. wost_estm), entering the
+// estimate with a minus sign: z on the Neumann boundary inside B(x, r) with
+// density 1 / W (neumann_pick, then uniform on the chosen primitive), counted
+// when it faces x (inside B there is no silhouette, so every Neumann point
+// there that faces x is on the star's boundary).
+//   <N> = G(x, z) h(z) W / alpha,  G = ln(r / |z - x|) / 2 pi  (2D),
+//                                      (1 / |z - x| - 1 / r) / 4 pi  (3D),
+// h the flux along the normal into the domain, alpha = 1/2 on a Neumann point.
+template <int D>
+__device__ __forceinline__ float neumann_term(const Walk<D> &w, const DevScene &sc, float r, uint32_t k0,
+                                              uint32_t k1, int *err, Visits *vis) {
+    float W;
+    const int js = neumann_pick<D>(sc.neu, w.x, r, w.pid, w.wid, (uint32_t)w.k, k0, k1, W, err, vis);
+    if (js < 0) return 0.f;
+    U4 u = philox(w.pid, w.wid, (uint32_t)w.k, P_NEU, k0, k1);
+    const float u0 = u01(u.x), u1 = u01(u.y);
+    float z[3];
+    if (D == 2) {
+        const float4 p = ldn(sc.neu.prims + js);
+        z[0] = (1.f - u0) * p.x + u0 * p.z;
+        z[1] = (1.f - u0) * p.y + u0 * p.w;
+    } else {
+        float a[3], b[3], c[3];
+        load_tri(sc.neu.prims, js, a, b, c);
+        const float su = sqrtf(u0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) z[i] = (1.f - su) * a[i] + su * (1.f - u1) * b[i] + su * u1 * c[i];
+    }
+    float dz[D], dd2 = 0.f, facing = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        dz[i] = z[i] - w.x[i];
+        dd2 += dz[i] * dz[i];
+        facing += dz[i] * __ldg(sc.nin_neu + (size_t)js * D + i);   // normals by leaf slot
+    }
+    const float dd = sqrtf(dd2);
+    if (!(dd > 0.f) || !(dd < r) || !(facing < 0.f)) return 0.f;
+    const float G = D == 2 ? logf(r / dd) * (0.5f / WOST_PI) : (1.f / dd - 1.f / r) * (0.25f / WOST_PI);
+    return G * eval_fn<D>(sc.h, z) * W * (w.prim >= 0 ? 2.f : 1.f);
+}
+
+// Steps 1-3.  Returns true if the walk ended (its value already added;
+// term_value 0 after a lost roulette draw).  On return false: r (star
+// radius) and S (this step's source and Neumann terms, times the step's
+// roulette scale, as the suffix pass of a recorded walk takes them).
 template <int D>
 __device__ __forceinline__ bool step_geometry(Walk<D> &w, const StepEnv &a, float &r, float &S,
                                               float &term_value, bool &truncated, Visits *vis) {
@@ -138,6 +202,14 @@ __device__ __forceinline__ bool step_geometry(Walk<D> &w, const StepEnv &a, floa
         truncated = !shell;
         return true;
     }
+    if (roulette_on(a, w.k)) {
+        if (!roulette_survives(a, w.pid, w.wid, w.k)) {
+            term_value = 0.f;
+            truncated = false;
+            return true;
+        }
+        w.T *= 1.f / a.rr_q;
+    }
     float bs = RD * RD;
     closest_silhouette<D>(sc.sil, w.x, sc.tau, bs, a.err, vis, sc.sil_cones);
     float R = fminf(sqrtf(bs), RD);
@@ -162,8 +234,13 @@ __device__ __forceinline__ bool step_geometry(Walk<D> &w, const StepEnv &a, floa
             for (int i = 0; i < D; ++i) y[i] = w.x[i] + rho * vs[i];
             S = -(r * r / (2.f * D)) * eval_fn<D>(sc.f, y);
         }
+        if (!sc.has_flux) w.acc += w.T * S;
+    }
+    if (sc.has_flux) {
+        S -= neumann_term<D>(w, sc, r, a.key0, a.key1, a.err, vis);
         w.acc += w.T * S;
     }
+    S *= roulette_scale(a, w.k);
     return false;
 }
 

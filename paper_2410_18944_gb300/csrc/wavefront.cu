@@ -163,7 +163,7 @@ __device__ __forceinline__ void wf_step_body(const Src &src, const WsOpts &o, co
                 const float n2 = onN && D == 3 ? w.n[D - 1] : 0.f;
                 rr[0] = make_float4(w.x[0], w.x[1], D == 3 ? w.x[D - 1] : 0.f, nu[0]);
                 rr[1] = make_float4(nu[1], D == 3 ? nu[D - 1] : 0.f, onN ? w.n[0] : 0.f, onN ? w.n[1] : 0.f);
-                rr[2] = make_float4(n2, ptil, wgt, Sx);
+                rr[2] = make_float4(n2, ptil, wgt * roulette_scale(env, w.k), Sx);
             }
             w.T *= wgt;
             step_move<D>(w, env, nu, r, &vis);

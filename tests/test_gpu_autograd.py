@@ -96,3 +96,23 @@ def test_optimisation_through_the_function_lowers_the_loss(mods):
         losses.append(loss.item())
     assert np.all(np.isfinite(losses))
     assert losses[-1] < losses[0]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_forward_computes_the_loss_only(mods, dim):
+    # forward runs the kernel's loss-only mode: the same loss as the full
+    # gradient pass, also under no_grad, and it leaves the field's gradient
+    # buffers alone (backward computes them)
+    api, ag = mods
+    F, OF, recs, tens = _setup(api, dim, 50 + dim, positive=False)
+    with torch.no_grad():
+        l0 = ag.field_loss(F, *tens)
+    assert l0.device.type == "cuda" and not l0.requires_grad
+    lg, _ = F.train_grad()
+    assert float(l0) == pytest.approx(lg, rel=1e-6)
+    loss = ag.field_loss(F, *tens)
+    assert float(loss) == pytest.approx(lg, rel=1e-6)
+    loss.backward()
+    g_ref = F.train_grad()[1]
+    for t, k in zip(tens, ("grid", "W1", "W2", "W3", "b3")):
+        assert np.allclose(t.grad.cpu().numpy(), g_ref[k], rtol=1e-5, atol=1e-7 * np.abs(g_ref[k]).max())

@@ -96,72 +96,6 @@ def test_closest_point_3d_parity(api):
     assert len(mism) <= 0.1 * len(pts)
 
 
-def _neumann_vertex_keys(sc):
-    return np.unique(sc.prims[sc.bc == 1].ravel())
-
-
-def _neumann_edge_keys(sc):
-    f = sc.prims[sc.bc == 1]
-    e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]])
-    e = np.sort(e, axis=1)
-    u = np.unique(e, axis=0)
-    return u[:, 0].astype(np.int64) * len(sc.verts) + u[:, 1]
-
-
-@pytest.mark.parametrize("dim", [2, 3])
-def test_silhouette_parity(api, dim):
-    if dim == 2:
-        sc = wi.star_polyline(512, seed=7, neumann_frac=0.6)
-        keys = _neumann_vertex_keys(sc)
-        pts = np.random.default_rng(2).uniform(-1.2, 1.2, (4000, 2))
-    else:
-        sc = wi.displaced_icosphere(subdiv=2, seed=4, neumann_frac=0.5, with_source=False)
-        keys = _neumann_edge_keys(sc)
-        pts = np.random.default_rng(3).uniform(-0.9, 0.9, (500, 3))
-    S, O = api.Scene(sc), oracle.Scene(sc)
-    gk, gd = S.query_silhouette(pts)
-    oe, od = O.closest_silhouette(pts)
-    ok_key = keys[oe]
-    same_d = np.abs(gd - od) <= 1e-6 * O.scale + 2e-7 * od
-    # equal distances with different elements are ties at a shared vertex
-    # (two silhouette edges meeting there); different distances only where
-    # the FP32 front/back/edge-on classification flips (a thin band)
-    assert same_d.mean() >= 0.995, same_d.mean()
-    exact = (gk == ok_key) & same_d
-    print(f"silhouette dim={dim}: same distance {same_d.mean():.4f}, same element {exact.mean():.4f}")
-    assert exact.mean() >= (0.99 if dim == 2 else 0.9)
-
-
-@pytest.mark.parametrize("dim", [2, 3])
-def test_ray_parity(api, dim):
-    if dim == 2:
-        sc = wi.star_polyline(512, seed=8, neumann_frac=0.7)
-        rng = np.random.default_rng(4)
-        org = rng.uniform(-0.6, 0.6, (4000, 2))
-        th = rng.uniform(0, 2 * np.pi, len(org))
-        dirs = np.stack([np.cos(th), np.sin(th)], 1)
-    else:
-        sc = wi.displaced_icosphere(subdiv=2, seed=9, neumann_frac=0.6, with_source=False)
-        rng = np.random.default_rng(5)
-        org = rng.uniform(-0.5, 0.5, (600, 3))
-        dirs = rng.normal(size=(600, 3))
-        dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
-    tmax = rng.uniform(0.2, 2.0, len(org))
-    S, O = api.Scene(sc), oracle.Scene(sc)
-    gi, gt = S.query_ray(org, dirs, tmax)
-    oi, ot = O.ray_neumann(org, dirs, tmax)
-    agree = gi == oi
-    hit = agree & (oi >= 0)
-    assert np.all(np.abs(gt[hit] - ot[hit]) <= 1e-5 * (1 + ot[hit]))
-    assert agree.mean() >= 0.998, agree.mean()
-    # skip semantics: re-cast from the hit point, skipping the hit primitive
-    h = np.nonzero(hit)[0][:200]
-    o2 = org[h] + ot[h, None] * dirs[h]
-    gi2, _ = S.query_ray(o2, dirs[h], 3.0, skip=gi[h])
-    oi2, _ = O.ray_neumann(o2, dirs[h], 3.0, skip=oi[h])
-    assert (gi2 == oi2).mean() >= 0.98
-
-
 # ---------------------------------------------------------------------------
 # vMF mixtures
 # ---------------------------------------------------------------------------
@@ -305,7 +239,7 @@ def test_plain_walk_closed_form(api, name):
     z = (m - ex) / np.sqrt(v)
     assert st["walks"] == n * len(pts)
     assert st["truncated"] == 0
-    assert np.all(np.abs(z) < 4.5), z
+    assert np.all(np.abs(z) < 4.0), z
 
 
 def test_plain_walk_vs_oracle_star(api):
@@ -371,13 +305,13 @@ def test_guided_frozen_field_vs_closed_form_and_oracle(api, dim, reflect):
     m, v, st = api.solve(S, pts, n, eps=1e-3, maxsteps=1024, seed=7, guided=True, field=F, reflect=reflect)
     ex = wi.eval_fn(sc.exact, pts)
     z = (m - ex) / np.sqrt(v)
-    assert np.all(np.abs(z) < 4.5), z
+    assert np.all(np.abs(z) < 4.0), z
     no = 1024
     r = oracle.solve(O, oracle.make_params(eps=1e-3, maxsteps=1024, seed=7, guided=1, reflect=reflect), pts, 0, no,
                      field=OF)
     om, ov = oracle.mean_var(r["sum"], r["sum2"], no)
     zo = (m - om) / np.sqrt(v + ov)
-    assert np.all(np.abs(zo) < 4.5), zo
+    assert np.all(np.abs(zo) < 4.0), zo
 
 
 # ---------------------------------------------------------------------------
@@ -478,7 +412,7 @@ def test_online_training_in_minibatches(api):
     assert st2["train_steps"] == 8
     ex = wi.eval_fn(sc.exact, pts)
     z = (m - ex) / np.sqrt(v)
-    assert np.all(np.isfinite(m)) and np.all(np.abs(z) < 4.5), z
+    assert np.all(np.isfinite(m)) and np.all(np.abs(z) < 4.0), z
 
 
 def test_online_training_runs_and_stays_unbiased(api):
@@ -492,7 +426,7 @@ def test_online_training_runs_and_stays_unbiased(api):
     assert st["train_steps"] == 16
     ex = wi.eval_fn(sc.exact, pts)
     z = (m - ex) / np.sqrt(v)
-    assert np.mean(np.abs(z) < 4.5) > 0.98
+    assert np.mean(np.abs(z) < 4.0) > 0.98
     p = F.get_params()
     assert np.all(np.isfinite(p["W1"])) and np.all(np.isfinite(p["grid"]))
 
