@@ -1,18 +1,29 @@
 #!/usr/bin/env python
 """Throughput benchmark of guided walk on stars on GB300.
 
-Workload (one "step" = one full solve, every hot-path stage included):
-2D Poisson/Laplace with mixed boundary conditions -- a seeded star-shaped
-polyline of 4096 segments (r = 1 + 0.3 sum of 5 Fourier modes), a contiguous
-zero-flux Neumann arc on 40% of it, Dirichlet data x^2 - y^2 elsewhere; a
-512 x 512 grid over the bounding box masked to the interior; 32 walks per
-point in 32 batches of one walk per point; guided sampling from the hash-grid
-+ MLP vMF mixture field with learnable MIS selection, trained after every
-batch (fused tcgen05 backward + Adam); eps = 1e-3, at most 128 steps per walk.
+Headline workload (the largest single-GPU configuration): 3D Laplace with
+mixed Dirichlet / zero-flux Neumann boundary on a seeded genus-3 solid -- a
+sphere displaced by 0.15 Perlin noise minus three smoothly rimmed tunnels,
+993,640 triangles by surface nets -- with a 30% Neumann cap and Dirichlet
+data g = 1/|x - c|; queries on the 1024 x 1024 slice z = 0 masked inside
+(510,479 points) at 128 walks per point; guided sampling from the 3D
+hash-grid + MLP vMF mixture field with learned MIS selection, trained online
+after every batch of one walk per point in minibatches of 2^18 records
+(fused tcgen05 backward + Adam).
+
+One "step" is one training round of the full slice: one walk per point
+(510,479 walks, every hot-path stage) followed by that batch's Adam steps.
+W rounds warm up, K rounds are timed (CUDA events on the launching stream),
+and the remaining rounds of the 128-walk solve run untimed to complete the
+estimate for the equal-time relMSE.  The BVHs (about 300 MB) and the
+batches are larger than L2, so no flush is needed.
 
 Metric: walk-steps/s (loop iterations of all walks, terminal step included),
-whole job over all ranks.  Timed with CUDA events on the launching stream;
-the L2 cache is flushed (a 512 MiB write) before every timed step.
+whole job over all ranks.  The line also carries the equal-time relMSE of
+guided vs plain WoSt on a seeded 4096-point subset, and extra lines for the
+2D star (4096 segments, 512 x 512 grid, 32 walks/point), the 81,920-triangle
+icosphere with Gaussian sources (256 x 256 slice, 64 walks/point) and 64
+uneven 2D scenes in one persistent launch per round under a CUDA graph.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -25,7 +36,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -40,25 +50,73 @@ import numpy as np  # noqa: E402
 
 METRIC = "walk-steps/s and equal-time relMSE: guided vs plain WoSt on one GB300"
 UNIT = "walk-steps/s"
-WORKLOAD = dict(workload="2D mixed Dirichlet/Neumann guided WoSt: star polyline 4096 segments, 40% zero-flux "
-                         "Neumann arc, g = x^2 - y^2, 512x512 grid masked inside, 32 walks/point, online training "
-                         "after every batch, 16-level 2^16-entry FP16 hash grid + 32-64-64-33 BF16 MLP, K = 8",
-                nseg=4096, grid=512, spp=32, eps=1e-3, maxsteps=128, l2="flushed (512 MiB write) before each step")
+DTYPE = "f32 geometry, bf16 MLP, f64 accumulators"
+
+WORKLOADS = {
+    "genus3": dict(workload="3D mixed Dirichlet/Neumann Laplace guided WoSt with learned MIS selection: genus-3 "
+                            "solid (sphere displaced by 0.15 Perlin noise minus three smoothly rimmed tunnels, "
+                            "993,640 triangles by surface nets), 30% Neumann cap, g = 1/|x - c|, 1024x1024 slice "
+                            "z = 0 masked inside, 128 walks/point, online training after every batch in minibatches "
+                            "of 2^18 records, 16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 MLP, K = 8",
+                   dim=3, grid=1024, spp=128, eps=1e-3, maxsteps=128, train_samples=1 << 18, subset=4096,
+                   ref_factor=64, step="one training round: one walk per point of the slice + its Adam steps",
+                   l2="inputs larger than L2 (about 300 MB of BVH, 510k-walk batches); no flush"),
+    "sphere3d": dict(workload="3D mixed Dirichlet/Neumann Poisson guided WoSt: icosphere 81,920 triangles displaced "
+                              "by 0.15 Perlin noise, 30% Neumann cap, f = 4 Gaussians (sigma 0.1), g = 1/|x - c|, "
+                              "256x256 slice z = 0 masked inside, 64 walks/point, online training after every batch "
+                              "in minibatches of 2^18 records, 16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 "
+                              "MLP, K = 8",
+                     dim=3, grid=256, spp=64, eps=1e-3, maxsteps=128, train_samples=1 << 18, subset=4096,
+                     ref_factor=64, step="one training round: one walk per point + its Adam steps",
+                     l2="flushed (512 MiB write) before each step"),
+    "star2d": dict(workload="2D mixed Dirichlet/Neumann guided WoSt: star polyline 4096 segments, 40% zero-flux "
+                            "Neumann arc, g = x^2 - y^2, 512x512 grid masked inside, 32 walks/point, online training "
+                            "after every batch in minibatches of 2^18 records, 16-level 2^16-entry FP16 hash grid + "
+                            "32-64-64-33 BF16 MLP, K = 8",
+                   dim=2, grid=512, spp=32, eps=1e-3, maxsteps=128, train_samples=1 << 18, subset=0,
+                   ref_factor=16, step="one training round: one walk per point + its Adam steps",
+                   l2="flushed (512 MiB write) before each step"),
+    "batch64": dict(workload="64 independent 2D star scenes (256-16384 segments log-uniform, Neumann fraction "
+                             "U(0.2, 0.5), 1k-256k points and 8-128 walks per point log-uniform), one persistent "
+                             "launch per training round under a CUDA graph, guided with online training per scene "
+                             "(and the plain batch for comparison)",
+                    dim=2, scenes=64, eps=1e-3, maxsteps=128, step="one replay of the whole batch's graph",
+                    l2="flushed (512 MiB write) before each step"),
+}
+HEADLINE = "genus3"
 
 
 def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def make_workload(res=512):
+def make_workload(key):
     import wost_inputs as wi
-    sc, pts = wi.config_star_guided(res=res)
-    return sc, pts
+    W = WORKLOADS[key]
+    if key == "genus3":
+        return wi.config_genus3(res=W["grid"])
+    if key == "sphere3d":
+        return wi.config_3d_guided(res=W["grid"])
+    return wi.config_star_guided(res=W["grid"])
 
 
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
+def smi_gpu_id(torch, dev_index):
+    """The nvidia-smi id of a torch device: its UUID (robust to
+    CUDA_VISIBLE_DEVICES remapping), else the visible-device mapping."""
+    try:
+        u = str(torch.cuda.get_device_properties(dev_index).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [x.strip() for x in vis.split(",") if x.strip()]
+    return ids[dev_index] if dev_index < len(ids) else str(dev_index)
+
+
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -136,41 +194,55 @@ def measured_peaks():
         return {}
 
 
+def load_profile(name):
+    """Per-walk-step counters of a kernel's ncu capture (profiles/*.json)."""
+    try:
+        return json.load(open(os.path.join(ROOT, "profiles", name)))
+    except (OSError, ValueError):
+        return None
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample of the same workload)
 # ---------------------------------------------------------------------------
-def oracle_rate(sc, pts, field_params, seconds=12.0, seed=3, guided=True):
-    """Walk-steps/s of the FP64 oracle on the host cores: guided walks (field
-    frozen at the given parameters) over a seeded subsample of the points,
-    repeated until about `seconds` of CPU time has been spent."""
+def oracle_rate(sc, pts, field_params, W, seconds=12.0, seed=3, guided=True, what="the same scene"):
+    """Walk-steps/s of the FP64 oracle on all host cores: guided walks (field
+    frozen at the given parameters) over seeded subsamples of the points,
+    one walk per point per pass, until about `seconds` have been spent."""
     import oracle
     import wost_inputs as wi
     nth = os.cpu_count() or 1
     O = oracle.Scene(sc)
     OF = oracle.Field(oracle.FieldParams(**field_params)) if guided else None
-    prm = oracle.make_params(eps=WORKLOAD["eps"], maxsteps=WORKLOAD["maxsteps"], guided=int(guided), seed=seed,
-                             nthreads=nth)
-    sample = wi.subsample(pts, 4 * nth * 16, seed=1)
-    steps = 0
-    walks = 0
+    prm = oracle.make_params(eps=W["eps"], maxsteps=W["maxsteps"], guided=int(guided), seed=seed, nthreads=nth)
+    steps = walks = passes = 0
+    n = nth
     t0 = time.perf_counter()
-    w = 0
-    while time.perf_counter() - t0 < seconds:
-        r = oracle.solve(O, prm, sample, w, 1, field=OF)
+    while True:
+        sample = wi.subsample(pts, n, seed=1 + passes)
+        t1 = time.perf_counter()
+        r = oracle.solve(O, prm, sample, passes, 1, field=OF)
+        dt1 = time.perf_counter() - t1
         steps += r["steps"]
         walks += len(sample)
-        w += 1
+        passes += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+        # grow the pass while it is short, never past the remaining budget
+        if dt1 < 0.25 * (seconds - el):
+            n = min(len(pts), 2 * n)
     dt = time.perf_counter() - t0
-    return steps / dt, dict(cores=nth, sample=f"{len(sample)} seeded grid points x {w} walks ({walks} walks, "
-                                               f"{steps} walk-steps, {dt:.1f} s) of the same scene, guided with "
-                                               f"the initial field frozen (no training step)")
+    return steps / dt, dict(cores=nth, sample=f"{walks} walks ({passes} passes of one walk at seeded subsets of the "
+                                              f"query points, {steps} walk-steps, {dt:.1f} s) of {what}, "
+                                              f"{'guided with the field frozen' if guided else 'plain'}")
 
 
-def field_params_dict(F, lo, hi):
+def field_params_dict(F, lo, hi, dim):
     import wost_inputs as wi
     p = F.get_params()
     d = F.desc
-    return dict(dim=2, K=d.K, L=d.levels, log2T=d.log2_table, F=d.features, H=d.hidden, base_res=d.base_res,
+    return dict(dim=dim, K=d.K, L=d.levels, log2T=d.log2_table, F=d.features, H=d.hidden, base_res=d.base_res,
                 max_res=d.max_res, lo=np.asarray(lo, float), hi=np.asarray(hi, float),
                 grid=wi.round_to_fp16(p["grid"]), W1=wi.round_to_bf16(p["W1"]), W2=wi.round_to_bf16(p["W2"]),
                 W3=wi.round_to_bf16(p["W3"]), b3=p["b3"].astype(float))
@@ -184,22 +256,25 @@ def run_reference(args):
     if rank != 0:
         return 0
     import wost_inputs as wi
-    sc, pts = make_workload()
+    key = args.workload if args.workload in ("genus3", "sphere3d", "star2d") else HEADLINE
+    W = WORKLOADS[key]
+    sc, pts = make_workload(key)
     # the field the oracle walks with: the library's default initialisation
-    # is not available without a GPU, so use a seeded field of the same shape
+    # needs the GPU, so a seeded field of the same shape
     lo, hi = sc.padded_bbox()
-    fp = wi.random_field_params(2, 1, lo, hi, grid_scale=1e-4, w_scale=1.0)
-    per = []
-    info = None
+    fp = wi.random_field_params(W["dim"], 1, lo, hi, log2T=16 if W["dim"] == 2 else 19, grid_scale=1e-4,
+                                w_scale=1.0)
+    per, info = [], None
     for i in range(args.warmup + args.steps):
-        rate, info = oracle_rate(sc, pts, fp, seconds=args.ref_seconds, seed=10 + i)
+        rate, info = oracle_rate(sc, pts, fp, W, seconds=args.ref_seconds, seed=10 + i,
+                                 what=f"the {key} workload")
         if i >= args.warmup:
             per.append(rate)
     value = statistics.mean(per)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * args.ref_seconds, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, reference_sample=info["sample"]), "impl": "reference",
+            "config": dict(W, reference_sample=info["sample"]), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
                              "sample": info["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -210,6 +285,308 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+class Ctx:
+    """Device, stream, L2 flush buffer and the API modules of one rank."""
+
+    def __init__(self, torch, api, wi, dev):
+        self.torch, self.api, self.wi, self.dev = torch, api, wi, dev
+        self.stream = torch.cuda.current_stream()
+        self.flush_buf = None
+
+    def flush(self):
+        if self.flush_buf is None:
+            self.flush_buf = self.torch.empty(128 * 1024 * 1024, dtype=self.torch.float32, device=self.dev)
+        self.flush_buf.zero_()
+
+    def events(self):
+        E = self.torch.cuda.Event
+        return E(enable_timing=True), E(enable_timing=True)
+
+    def timed(self, fn, flush=False):
+        if flush:
+            self.flush()
+        self.torch.cuda.synchronize()
+        e0, e1 = self.events()
+        e0.record(self.stream)
+        out = fn()
+        e1.record(self.stream)
+        self.torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+
+def measure_l2_copy_gbs(ctx):
+    """L2-resident copy bandwidth (read + write bytes), measured here: a
+    24 MiB -> 24 MiB copy repeated 200 times stays in the 129 MB L2."""
+    torch = ctx.torch
+    n = 6 * 1024 * 1024
+    a = torch.ones(n, dtype=torch.float32, device=ctx.dev)
+    b = torch.empty_like(a)
+    for _ in range(20):
+        b.copy_(a)
+    ms, _ = ctx.timed(lambda: [b.copy_(a) for _ in range(200)])
+    return 200 * 2 * 4 * n / (ms / 1000.0) / 1e9
+
+
+def roofline(stats, key, walk_kernel, l2_gbs):
+    """Roofline of the dominant kernel (the guided walk kernel): algorithmic
+    bytes per launch (visited BVH nodes and primitives, hash-grid corner
+    reads, start points, FP64 accumulators, training records; counted in the
+    kernel) over its average launch time (library CUDA events on the
+    launching stream).  The serving level's figures (L2 bytes and issue
+    activity per walk-step) come from the kernel's ncu capture on a small
+    case of the same workload, scaled by this run's walk-steps per launch."""
+    walk_ms = sum(s["ms_walk"] for s in stats)
+    launches = sum(s["walk_launches"] for s in stats)
+    steps = sum(s["walk_steps"] for s in stats)
+    alg = sum(s["alg_bytes"] for s in stats)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    sec = (walk_ms / launches) / 1000.0
+    achieved = (alg / launches) / sec / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "kernel": walk_kernel, "peak_source": src,
+            "alg_bytes_per_walk_step": alg / steps, "walk_steps_per_launch": steps / launches}
+    prof = load_profile(f"{key}_walk_counters.json")
+    if prof:
+        per = steps / launches
+        roof["traffic"] = prof["dram_bytes_per_walk_step"] * per
+        lts = prof["lts_bytes_per_walk_step"] * per / sec / 1e9
+        roof["serving_level"] = {
+            "level": "L2", "achieved": lts, "unit": "GB/s", "peak": l2_gbs, "peak_source": "measured L2 copy",
+            "frac": lts / l2_gbs, "lts_bytes_per_walk_step": prof["lts_bytes_per_walk_step"],
+            "dram_bytes_per_walk_step": prof["dram_bytes_per_walk_step"],
+            "l1_bytes_per_walk_step": prof.get("l1_bytes_per_walk_step"),
+            "issue_active_frac": prof.get("issue_active_frac"),
+            "threads_per_inst": prof.get("threads_per_inst"),
+            "capture": prof.get("capture")}
+    return roof
+
+
+def guided_rounds_line(ctx, key, args, rank=0, world=1, full=True):
+    """One single-scene workload, round by round: W warm-up rounds, K timed
+    rounds, then (full) the remaining rounds of the solve and the equal-time
+    relMSE, the end-to-end rounds with host buffers and the oracle's rate."""
+    torch, api, wi = ctx.torch, ctx.api, ctx.wi
+    W = WORKLOADS[key]
+    dim, spp = W["dim"], W["spp"]
+    sc, pts_np = make_workload(key)
+    S = api.Scene(sc)
+    lo, hi = S.bbox()
+    F = api.Field(dim, lo, hi, seed=1 + rank)
+    init = F.get_params()
+    pts = torch.tensor(pts_np, dtype=torch.float64, device=ctx.dev)
+    npts = len(pts_np)
+    seed = 1000 + 7919 * rank
+    common = dict(eps=W["eps"], maxsteps=W["maxsteps"], stream=ctx.stream)
+    gkw = dict(guided=True, field=F, train=1, train_until_wpp=256, train_samples=W["train_samples"], seed=seed,
+               **common)
+    flush = "flush" in W["l2"]
+    nsub = W["subset"] if W["subset"] and W["subset"] < npts else npts
+    sub = np.sort(np.random.default_rng(7).choice(npts, nsub, replace=False)) if nsub < npts else np.arange(npts)
+    sub_t = torch.tensor(sub, device=ctx.dev)
+    acc = torch.zeros(nsub, dtype=torch.float64, device=ctx.dev)
+
+    def round_(r):
+        ms, (m, v, st) = ctx.timed(lambda: api.solve(S, pts, 1, walk_begin=r, **gkw), flush=flush)
+        acc.add_(m[sub_t])
+        return ms, st
+
+    warm = min(args.warmup, spp - 1)
+    nsteps = max(1, min(args.steps, spp - warm))
+    for r in range(warm):
+        round_(r)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    per_ms, stats = [], []
+    with ClockSampler(smi_gpu_id(torch, torch.cuda.current_device())) as clk:
+        for r in range(warm, warm + nsteps):
+            ms, st = round_(r)
+            per_ms.append(ms)
+            stats.append(st)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    total_ms, steps_all = combine_ranks(sum(per_ms), sum(s["walk_steps"] for s in stats), ctx.dev)
+    value = steps_all / (total_ms / 1000.0)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": nsteps, "warmup": warm,
+            "ms_per_step": total_ms / nsteps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE, "data": "synthetic",
+            "config": dict(W, points=npts, parallelism=f"replicas x{world}"), "clocks": clk.summary(),
+            "gpu_launches": int(round(sum(s["kernel_launches"] for s in stats) / len(stats)))}
+    if not full or rank != 0:
+        return line, None
+    # the rest of the solve (untimed): every round of the spp-walk estimate
+    for r in range(warm + nsteps, spp):
+        round_(r)
+    guided_s = (sum(per_ms) / nsteps) * spp / 1000.0     # a full solve at the timed rate
+    # plain walks: time per walk over the whole point set, in one launch of
+    # at least 4 M walks (as a plain solve would run them) or all spp walks
+    nplain = min(spp, max(2, -(-(1 << 22) // npts)))
+    api.solve(S, pts, 1, seed=91, **common)
+    pms, (mp_, vp_, stp) = ctx.timed(lambda: api.solve(S, pts, nplain, seed=92, **common), flush=flush)
+    plain_rate = stp["walk_steps"] / (pms / 1000.0)
+    plain_s = pms / 1000.0 * spp / nplain                 # a full plain solve at spp walks
+    psub = pts[sub_t].contiguous()
+    guided_mean = (acc / spp).cpu().numpy()
+    relmse = None
+    if not args.no_relmse:
+        spp_ref = W["ref_factor"] * spp
+        ref, rvar, _ = api.solve(S, psub, spp_ref, seed=424242, **common)
+        ref, rvar = ref.cpu().numpy(), rvar.cpu().numpy()
+
+        def rel(u):
+            return float(np.mean((u - ref) ** 2 / (ref ** 2 + 1e-2)))
+
+        def rel_c(u):      # the reference's own variance removed (an unbiased estimate)
+            return float(np.mean(((u - ref) ** 2 - rvar) / (ref ** 2 + 1e-2)))
+        spp_eq = max(1, int(spp * guided_s / plain_s))
+        m_eq = api.solve(S, psub, spp_eq, seed=515151, **common)[0].cpu().numpy()
+        m_sp = api.solve(S, psub, spp, seed=616161, **common)[0].cpu().numpy()
+        relmse = {"guided": rel(guided_mean), "plain_equal_time": rel(m_eq), "plain_equal_spp": rel(m_sp),
+                  "plain_spp_at_equal_time": spp_eq,
+                  "equal_time_ratio_plain_over_guided": rel(m_eq) / rel(guided_mean),
+                  "corrected": {"guided": rel_c(guided_mean), "plain_equal_time": rel_c(m_eq),
+                                "plain_equal_spp": rel_c(m_sp),
+                                "equal_time_ratio_plain_over_guided": rel_c(m_eq) / rel_c(guided_mean),
+                                "note": "the reference's own per-point variance subtracted"},
+                  "variance_reduction_equal_spp": rel_c(m_sp) / rel_c(guided_mean),
+                  "guided_over_plain_cost_per_walk": guided_s / plain_s,
+                  "subset_points": nsub, "reference": f"plain WoSt, {spp_ref} walks/point on the subset",
+                  "guided_s_per_solve": guided_s, "plain_s_per_solve": plain_s}
+    # end to end through the C ABI with host buffers: pinned host points in,
+    # mean and variance out, every round a wost_solve call
+    pts_host = torch.tensor(pts_np, dtype=torch.float64).pin_memory().numpy()
+    F.set_params(init["grid"], init["W1"], init["W2"], init["W3"], init["b3"])
+    e2e_steps, e2e_s = 0, 0.0
+    for r in range(3):
+        if flush:
+            ctx.flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m, v, st = api.solve(S, pts_host, 1, walk_begin=r, guided=True, field=F, train=1, train_until_wpp=256,
+                             train_samples=W["train_samples"], seed=seed + 1, eps=W["eps"], maxsteps=W["maxsteps"])
+        e2e_s += time.perf_counter() - t0
+        e2e_steps += st["walk_steps"]
+    line["e2e"] = {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(npts * dim * 8),
+                   "d2h_bytes_per_step": int(npts * 2 * 8)}
+    kern = f"guided_walk_kernel<{dim}>"
+    line["roofline"] = roofline(stats, key, kern, ctx.l2_gbs)
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, info = oracle_rate(sc, pts_np[sub] if nsub < npts else pts_np, field_params_dict(F, lo, hi, dim), W,
+                                 seconds=args.cpu_seconds, what=f"the {key} workload")
+        cpu = {"value": rate, "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": info["sample"]}
+    line["cpu_baseline"] = cpu
+    line["breakdown"] = {"walk_ms_per_step": sum(s["ms_walk"] for s in stats) / len(stats),
+                         "train_ms_per_step": sum(s["ms_train"] for s in stats) / len(stats),
+                         "walk_steps_per_step": sum(s["walk_steps"] for s in stats) / len(stats),
+                         "records_per_step": sum(s["records"] for s in stats) / len(stats),
+                         "adam_steps_per_step": sum(s["train_steps"] for s in stats) / len(stats)}
+    line["plain_walk_steps_per_s"] = plain_rate
+    line["relmse"] = relmse
+    return line, F
+
+
+def decode_line(ctx, F, dim, lo, hi):
+    """The tensor-core decode on its own: 4 Mi positions through
+    wost_field_decode (hash-grid encode + three tcgen05 BF16 MMAs per 128-row
+    tile), device buffers, CUDA events on the stream."""
+    torch, api = ctx.torch, ctx.api
+    ndec = 1 << 22
+    g = torch.Generator(device=ctx.dev)
+    g.manual_seed(5)
+    lo_t = torch.tensor(lo, dtype=torch.float64, device=ctx.dev)
+    hi_t = torch.tensor(hi, dtype=torch.float64, device=ctx.dev)
+    pts = lo_t + (hi_t - lo_t) * torch.rand((ndec, dim), dtype=torch.float64, device=ctx.dev, generator=g)
+    out = torch.empty((ndec, F.nout), dtype=torch.float32, device=ctx.dev)
+    ex = api.exec_defaults(stream=ctx.stream)
+    for _ in range(3):
+        F.decode(pts, out=out, exec_=ex)
+    ms, _ = ctx.timed(lambda: F.decode(pts, out=out, exec_=ex), flush=True)
+    nout = (dim + 2) * 8 + 1
+    flop = 2.0 * (32 * 64 + 64 * 64 + 64 * nout)          # the method's FLOPs per decode (unpadded)
+    peak = measured_peaks().get("bf16_tflops")
+    tf = ndec * flop / (ms / 1000.0) / 1e12
+    return {"points": ndec, "ms": ms, "decodes_per_s": ndec / (ms / 1000.0), "bound": "tensor",
+            "achieved_tflops": tf, "peak_tflops": peak or 1900.0, "frac": tf / (peak or 1900.0),
+            "peak_source": "measured" if peak else "fallback", "flop_per_decode": flop,
+            "note": f"per point {flop / 1e3:.1f} kFLOP of BF16 MMA against {16 * 2 ** dim} hash-grid corner "
+                    "gathers (L2): the encode gathers, not the tensor pipe, set the decode time"}
+
+
+def batch_line(ctx, args):
+    """64 scenes in one persistent launch per training round under a CUDA
+    graph: guided (online training per scene) and plain."""
+    torch, api, wi = ctx.torch, ctx.api, ctx.wi
+    W = WORKLOADS["batch64"]
+    jobs = wi.config_batch()
+    scenes = [api.Scene(j.scene) for j in jobs]
+    pts = [torch.tensor(j.points, dtype=torch.float64, device=ctx.dev) for j in jobs]
+    plans, fields = {}, []
+    for guided in (True, False):
+        specs = []
+        for i, j in enumerate(jobs):
+            d = dict(scene=scenes[i], points=pts[i], nwalks=j.nwalks, seed=j.seed, eps=W["eps"], maxsteps=W["maxsteps"])
+            if guided:
+                lo, hi = scenes[i].bbox()
+                d["field"] = api.Field(2, lo, hi, seed=1 + i)
+                fields.append(d["field"])
+            specs.append(d)
+        plans[guided] = api.Batch(specs, guided=guided, train=1 if guided else 0)
+
+    def run(guided):
+        return ctx.timed(lambda: plans[guided].run(ctx.stream.cuda_stream), flush=True)
+    # one replay takes about 19 s (150 M walks, 2,741 training steps): one
+    # warm-up replay (the plan's autotuner already ran its calibration
+    # launches) and two timed ones
+    run(True)
+    per, stats = [], []
+    nsteps = max(1, min(args.steps, 2))
+    with ClockSampler(smi_gpu_id(torch, torch.cuda.current_device())) as clk:
+        for _ in range(nsteps):
+            ms, st = run(True)
+            per.append(ms)
+            stats.append(st)
+    pms, pst = run(False)
+    value = sum(s["walk_steps"] for s in stats) / (sum(per) / 1000.0)
+    # end to end: the points copied from pinned host memory into the plan's
+    # device inputs and every job's mean copied back, around each replay
+    host = [torch.tensor(j.points, dtype=torch.float64).pin_memory() for j in jobs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = 0
+    for _ in range(2):
+        for h, d in zip(host, pts):
+            d.copy_(h, non_blocking=True)
+        st = plans[True].run(ctx.stream.cuda_stream)
+        outs = [m.cpu() for m in plans[True].mean]
+        e2e_steps += st["walk_steps"]
+    e2e_s = time.perf_counter() - t0
+    npts = sum(len(j.points) for j in jobs)
+    for_roof = [dict(ms_walk=s["ms_walk"], walk_launches=s["walk_launches"], walk_steps=s["walk_steps"],
+                     alg_bytes=s["alg_bytes"]) for s in stats]
+    line = {"value": value, "unit": UNIT, "steps": nsteps, "ms_per_step": sum(per) / nsteps,
+            "config": dict(W, points=npts, walks=sum(len(j.points) * j.nwalks for j in jobs),
+                           plan={"guided": plans[True].info(), "plain": plans[False].info()}),
+            "clocks": clk.summary(), "plain_walk_steps_per_s": pst["walk_steps"] / (pms / 1000.0),
+            "gpu_launches": int(plans[True].info()["graph_nodes"]),
+            "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(npts * 2 * 8),
+                    "d2h_bytes_per_step": int(npts * 8)},
+            "roofline": roofline(for_roof, "batch64", "batch_guided_kernel<2>", ctx.l2_gbs)}
+    del outs
+    if not args.no_cpu_baseline:
+        j = jobs[0]
+        lo, hi = scenes[0].bbox()
+        rate, info = oracle_rate(j.scene, j.points, field_params_dict(fields[0], lo, hi, 2), W,
+                                 seconds=min(args.cpu_seconds, 5.0), what="the batch's first scene")
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                                "sample": info["sample"]}
+    return line
+
+
 def run_ours(args):
     import torch
     rank, world, local = env_rank()
@@ -218,348 +595,33 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
+    import wost_inputs as wi
     from paper_2410_18944_gb300 import api, build
     if rank == 0:
         build.build()
-    barrier()
-    sc, pts_np = make_workload()
-    S = api.Scene(sc)
-    lo, hi = S.bbox()
-    F = api.Field(2, lo, hi, seed=1 + rank)
-    init = F.get_params()
-    pts = torch.tensor(pts_np, dtype=torch.float64, device=dev)
-    npts = len(pts_np)
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)   # 512 MiB > L2
-    kw = dict(eps=WORKLOAD["eps"], maxsteps=WORKLOAD["maxsteps"], guided=True, field=F, train=1,
-              train_until_wpp=256, stream=stream)
-
-    def one_step(i, timed_events=None):
-        F.set_params(init["grid"], init["W1"], init["W2"], init["W3"], init["b3"])   # fresh field every step
-        flush.zero_()
-        torch.cuda.synchronize()
-        if timed_events is not None:
-            timed_events[0].record(stream)
-        m, v, st = api.solve(S, pts, WORKLOAD["spp"], seed=1000 * rank + i, **kw)
-        if timed_events is not None:
-            timed_events[1].record(stream)
-        last_mean[0] = m
-        return st
-
-    last_mean = [None]
-
-    for i in range(args.warmup):
-        one_step(i)
-    torch.cuda.synchronize()
-    barrier()
-    per_ms, stats = [], []
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            st = one_step(args.warmup + i, ev)
-            torch.cuda.synchronize()
-            per_ms.append(ev[0].elapsed_time(ev[1]))
-            stats.append(st)
-    barrier()
-    steps_local = sum(s["walk_steps"] for s in stats)
-    total_ms, steps_all = combine_ranks(sum(per_ms), steps_local, dev)
-    value = steps_all / (total_ms / 1000.0)
-
-    # end to end through the C ABI with host buffers (pinned points and
-    # outputs; H2D of the points and D2H of mean and variance inside)
-    pts_host = torch.tensor(pts_np, dtype=torch.float64).pin_memory()
-    e2e_steps, e2e_s = 0, 0.0
-    for i in range(max(1, min(args.steps, 3))):
-        F.set_params(init["grid"], init["W1"], init["W2"], init["W3"], init["b3"])
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        m, v, st = api.solve(S, pts_host.numpy(), WORKLOAD["spp"], seed=7000 + i, eps=WORKLOAD["eps"],
-                             maxsteps=WORKLOAD["maxsteps"], guided=True, field=F, train=1, train_until_wpp=256)
-        e2e_s += time.perf_counter() - t0
-        e2e_steps += st["walk_steps"]
-    e2e_value = world * e2e_steps / e2e_s
-
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    ctx = Ctx(torch, api, wi, dev)
+    ctx.l2_gbs = measure_l2_copy_gbs(ctx)
+    key = args.workload if args.workload in ("genus3", "sphere3d", "star2d") else HEADLINE
+    line, F = guided_rounds_line(ctx, key, args, rank, world, full=True)
     if rank != 0:
         return 0
-
-    # plain WoSt on the same workload (same grid, spp), for context
-    mp, vp, stp = api.solve(S, pts, WORKLOAD["spp"], seed=99, eps=WORKLOAD["eps"], maxsteps=WORKLOAD["maxsteps"],
-                            stream=stream)
-    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    flush.zero_()
-    torch.cuda.synchronize()
-    ev[0].record(stream)
-    mp, vp, stp = api.solve(S, pts, WORKLOAD["spp"], seed=98, eps=WORKLOAD["eps"], maxsteps=WORKLOAD["maxsteps"],
-                            stream=stream)
-    ev[1].record(stream)
-    torch.cuda.synchronize()
-    plain_rate = stp["walk_steps"] / (ev[0].elapsed_time(ev[1]) / 1000.0)
-
-    # the tensor-core decode on its own: 4 Mi positions through
-    # wost_field_decode (hash-grid encode + three tcgen05 BF16 MMAs per
-    # 128-row tile), device buffers, CUDA events on the stream
-    ndec = 1 << 22
-    g = torch.Generator(device=dev)
-    g.manual_seed(5)
-    lo_t = torch.tensor(lo, dtype=torch.float64, device=dev)
-    hi_t = torch.tensor(hi, dtype=torch.float64, device=dev)
-    dec_pts = lo_t + (hi_t - lo_t) * torch.rand((ndec, 2), dtype=torch.float64, device=dev, generator=g)
-    dec_out = torch.empty((ndec, F.nout), dtype=torch.float32, device=dev)
-    for _ in range(2):
-        F.decode(dec_pts, out=dec_out, exec_=api.exec_defaults(stream=stream))
-    flush.zero_()
-    torch.cuda.synchronize()
-    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    ev[0].record(stream)
-    F.decode(dec_pts, out=dec_out, exec_=api.exec_defaults(stream=stream))
-    ev[1].record(stream)
-    torch.cuda.synchronize()
-    dec_s = ev[0].elapsed_time(ev[1]) / 1000.0
-    flop_per = 2.0 * (32 * 64 + 64 * 64 + 64 * 48)       # padded output width 48
-    bf16_peak = measured_peaks().get("bf16_tflops")
-    dec_tflops = ndec * flop_per / dec_s / 1e12
-    decode = {"points": ndec, "ms": dec_s * 1e3, "decodes_per_s": ndec / dec_s, "bound": "tensor",
-              "achieved_tflops": dec_tflops, "peak_tflops": bf16_peak or 1900.0,
-              "frac": dec_tflops / (bf16_peak or 1900.0),
-              "peak_source": "measured" if bf16_peak else "fallback",
-              "note": "per point 18.4 kFLOP of BF16 MMA against 64 hash-grid corner gathers (L2): "
-                      "the encode gathers, not the tensor pipe, set the decode time"}
-
-    # equal-time relMSE (guided with training vs plain), against a plain
-    # reference at 16x the walks per point; relMSE = mean (u^ - u)^2 / (u^2 + 1e-2)
-    relmse = None
-    if not args.no_relmse:
-        guided_mean = last_mean[0].cpu().numpy()
-        spp_ref = 16 * WORKLOAD["spp"]
-        ref, _, _ = api.solve(S, pts, spp_ref, seed=424242, eps=WORKLOAD["eps"], maxsteps=WORKLOAD["maxsteps"],
-                              stream=stream)
-        ref = ref.cpu().numpy()
-
-        def rel(u):
-            return float(np.mean((u - ref) ** 2 / (ref ** 2 + 1e-2)))
-        t32 = stp["walk_steps"] / plain_rate          # seconds for 32 plain walks per point
-        guided_s = total_ms / args.steps / 1000.0
-        spp_eq = max(1, int(WORKLOAD["spp"] * guided_s / t32))
-        mp_eq, _, _ = api.solve(S, pts, spp_eq, seed=515151, eps=WORKLOAD["eps"], maxsteps=WORKLOAD["maxsteps"],
-                                stream=stream)
-        r_g, r_pe, r_ps = rel(guided_mean), rel(mp_eq.cpu().numpy()), rel(mp.cpu().numpy())
-        relmse = {"guided": r_g, "plain_equal_time": r_pe, "plain_equal_spp": r_ps, "plain_spp_at_equal_time": spp_eq,
-                  "equal_time_ratio_plain_over_guided": r_pe / r_g, "reference": f"plain WoSt, {spp_ref} walks/point",
-                  "guided_s_per_solve": guided_s}
-
-    # roofline of the dominant kernel (the guided walk kernel): algorithmic
-    # bytes per launch over its average launch time (library CUDA events on
-    # the same stream, summed over the timed steps)
-    walk_ms = sum(s["ms_walk"] for s in stats)
-    train_ms = sum(s["ms_train"] for s in stats)
-    walk_launches = sum(s["walk_launches"] for s in stats)
-    alg = sum(s["alg_bytes"] for s in stats)
-    peaks = measured_peaks()
-    hbm = peaks.get("hbm_gbs")
-    peak_src = "measured" if hbm else "fallback"
-    hbm = hbm or 6800.0
-    achieved = (alg / walk_launches) / ((walk_ms / walk_launches) / 1000.0) / 1e9
-    traffic = args.traffic
-    if traffic is None:
-        # DRAM bytes per walk-step of the walk kernel from its ncu capture,
-        # scaled to this run's walk-steps per launch
-        try:
-            tr = json.load(open(os.path.join(ROOT, "profiles", "guided_walk_traffic.json")))
-            traffic = tr["dram_bytes_per_walk_step"] * sum(s["walk_steps"] for s in stats) / walk_launches
-        except (OSError, ValueError, KeyError):
-            traffic = None
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": traffic, "kernel": "guided_walk_kernel<2>", "peak_source": peak_src,
-            "alg_bytes_per_walk_step": alg / sum(s["walk_steps"] for s in stats)}
-
-    cpu_rate, cpu_info = (None, {})
-    if not args.no_cpu_baseline:
-        cpu_rate, cpu_info = oracle_rate(sc, pts_np, field_params_dict(F, lo, hi), seconds=args.cpu_seconds)
-
-    launches = sum(s["kernel_launches"] for s in stats) // len(stats)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 geometry, bf16 MLP, f64 accumulators",
-            "data": "synthetic", "config": dict(WORKLOAD, points=npts, parallelism=f"replicas x{world}"),
-            "clocks": clk.summary(),
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(npts * 2 * 8),
-                    "d2h_bytes_per_step": int(npts * 2 * 8)},
-            "gpu_launches": launches,
-            "roofline": roof,
-            "cpu_baseline": ({"value": cpu_rate, "unit": UNIT, "cores": cpu_info.get("cores"), "kind": "oracle",
-                              "sample": cpu_info.get("sample")} if cpu_rate else None),
-            "breakdown": {"walk_ms_per_step": walk_ms / len(stats), "train_ms_per_step": train_ms / len(stats),
-                          "walk_steps_per_step": steps_local / len(stats),
-                          "records_per_step": sum(s["records"] for s in stats) / len(stats)},
-            "plain_walk_steps_per_s": plain_rate,
-            "decode": decode,
-            "relmse": relmse}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-WORKLOADS = {
-    "sphere3d": dict(workload="3D mixed Dirichlet/Neumann Poisson guided WoSt: icosphere 81,920 triangles displaced "
-                              "by 0.15 Perlin noise, 30% Neumann cap, f = 4 Gaussians (sigma 0.1), g = 1/|x - c|, "
-                              "256x256 slice z = 0 masked inside, 64 walks/point, online training after every batch "
-                              "in minibatches of 2^18 records, 16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 "
-                              "MLP, K = 8",
-                     grid=256, spp=64, eps=1e-3, maxsteps=128, train_samples=1 << 18,
-                     l2="flushed (512 MiB write) before each step"),
-    "genus3": dict(workload="3D mixed Dirichlet/Neumann Laplace guided WoSt with learned MIS selection: genus-3 "
-                            "solid (sphere displaced by 0.15 Perlin noise minus three smoothly rimmed tunnels, "
-                            "993,640 triangles by surface nets), 30% Neumann cap, g = 1/|x - c|, 1024x1024 slice "
-                            "z = 0 masked inside, 128 walks/point, online training after every batch in minibatches "
-                            "of 2^18 records, 16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 MLP, K = 8",
-                   grid=1024, spp=128, eps=1e-3, maxsteps=128, train_samples=1 << 18,
-                   l2="inputs larger than L2 (the BVHs and 1 M-walk batches); no flush"),
-    "batch64": dict(workload="64 independent 2D star scenes (256-16384 segments log-uniform, Neumann fraction "
-                             "U(0.2, 0.5), 1k-256k points and 8-128 walks per point log-uniform), one persistent "
-                             "launch per training round under a CUDA graph, guided with online training per scene "
-                             "(and the plain batch for comparison)",
-                    scenes=64, eps=1e-3, maxsteps=128, l2="flushed (512 MiB write) before each step"),
-}
-
-
-def run_workload_3d(args, W, api, wi, torch, dev, flush, stream):
-    """A 3D workload line: guided solves with online training (fresh field
-    each), the plain solve of the same size, and equal-time relMSE on a
-    seeded 4096-point subset against a plain reference at 64x the walks per
-    point (the oracle's brute-force geometry cannot reach a low-variance
-    reference on these meshes)."""
-    if args.workload == "sphere3d":
-        sc, pts_np = wi.config_3d_guided(res=W["grid"])
-    else:
-        sc, pts_np = wi.config_genus3(res=W["grid"])
-    S = api.Scene(sc)
-    lo, hi = S.bbox()
-    F = api.Field(3, lo, hi, seed=1)
-    init = F.get_params()
-    pts = torch.tensor(pts_np, dtype=torch.float64, device=dev)
-    rng = np.random.default_rng(7)
-    sub = np.sort(rng.choice(len(pts_np), min(4096, len(pts_np)), replace=False))
-    sub_t = torch.tensor(sub, device=dev)
-    psub = pts[sub_t].contiguous()
-    common = dict(eps=W["eps"], maxsteps=W["maxsteps"], stream=stream)
-
-    def timed(fn):
-        flush.zero_()
-        torch.cuda.synchronize()
-        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-        ev[0].record(stream)
-        out = fn()
-        ev[1].record(stream)
-        torch.cuda.synchronize()
-        return ev[0].elapsed_time(ev[1]), out
-
-    def guided(p, spp, seed):
-        F.set_params(init["grid"], init["W1"], init["W2"], init["W3"], init["b3"])
-        return api.solve(S, p, spp, seed=seed, guided=True, field=F, train=1, train_until_wpp=256,
-                         train_samples=W.get("train_samples", 0), **common)
-
-    big = W["spp"] * len(pts_np) > 20_000_000
-    steps = 1 if big else args.steps
-    # warm-up: full solves for the small workload, a 16k-point subset of the large one
-    wp = pts[:16384].contiguous() if big else pts
-    for i in range(args.warmup):
-        guided(wp, 2 if big else W["spp"], i)
-        api.solve(S, wp, 2 if big else W["spp"], seed=50 + i, **common)
-    ms_g, nsteps, stats = 0.0, 0, []
-    for i in range(steps):
-        t, (mg, _, st) = timed(lambda: guided(pts, W["spp"], 100 + i))
-        ms_g += t
-        nsteps += st["walk_steps"]
-        stats.append(st)
-    ms_p, (mp, _, stp) = timed(lambda: api.solve(S, pts, W["spp"], seed=999, **common))
-    guided_s = ms_g / steps / 1000.0
-    plain_s = ms_p / 1000.0
-    spp_ref = 64 * W["spp"]
-    ref = api.solve(S, psub, spp_ref, seed=424242, **common)[0].cpu().numpy()
-    spp_eq = max(1, int(W["spp"] * guided_s / plain_s))
-    mpe = api.solve(S, psub, spp_eq, seed=515151, **common)[0].cpu().numpy()
-
-    def rel(u):
-        return float(np.mean((u - ref) ** 2 / (ref ** 2 + 1e-2)))
-    r_g = rel(mg[sub_t].cpu().numpy())
-    r_ps = rel(mp[sub_t].cpu().numpy())
-    r_pe = rel(mpe)
-    line = {"metric": METRIC, "value": nsteps / (ms_g / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": steps,
-            "warmup": args.warmup, "ms_per_step": ms_g / steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 geometry, bf16 MLP, f64 accumulators", "data": "synthetic",
-            "config": dict(W, points=len(pts_np), warmup_points=len(wp)),
-            "plain_walk_steps_per_s": stp["walk_steps"] / plain_s,
-            "breakdown": {"walk_ms": sum(s["ms_walk"] for s in stats) / steps,
-                          "train_ms": sum(s["ms_train"] for s in stats) / steps,
-                          "train_steps": stats[-1]["train_steps"], "records_last_batch": stats[-1]["records"]},
-            "relmse": {"guided": r_g, "plain_equal_spp": r_ps, "plain_equal_time": r_pe,
-                       "plain_spp_at_equal_time": spp_eq, "equal_time_ratio_plain_over_guided": r_pe / r_g,
-                       "subset_points": len(sub), "reference": f"plain WoSt, {spp_ref} walks/point on the subset",
-                       "guided_s_per_solve": guided_s, "plain_s_per_solve": plain_s}}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def run_workload(args):
-    """Other workloads of the method (same metric and timing rules), for the
-    design notes: --workload sphere3d | genus3 | batch64 on one GPU."""
-    import torch
-    import wost_inputs as wi
-    from paper_2410_18944_gb300 import api, build
-    build.build()
-    W = WORKLOADS[args.workload]
-    dev = torch.device("cuda", 0)
-    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-    extra = {}
-    if args.workload in ("sphere3d", "genus3"):
-        return run_workload_3d(args, W, api, wi, torch, dev, flush, stream)
-    else:
-        jobs = wi.config_batch()
-        scenes = [api.Scene(j.scene) for j in jobs]
-        pts = [torch.tensor(j.points, dtype=torch.float64, device=dev) for j in jobs]
-        plans = {}
-        for guided in (True, False):
-            specs = []
-            for i, j in enumerate(jobs):
-                d = dict(scene=scenes[i], points=pts[i], nwalks=j.nwalks, seed=j.seed, eps=W["eps"],
-                         maxsteps=W["maxsteps"])
-                if guided:
-                    lo, hi = scenes[i].bbox()
-                    d["field"] = api.Field(2, lo, hi, seed=1 + i)
-                specs.append(d)
-            plans[guided] = api.Batch(specs, guided=guided, train=1 if guided else 0)
-        extra["plan"] = {("guided" if g else "plain"): p.info() for g, p in plans.items()}
-        extra["points"] = sum(len(j.points) for j in jobs)
-        extra["walks"] = sum(len(j.points) * j.nwalks for j in jobs)
-
-        def solve(i, guided=True):
-            flush.zero_()
-            torch.cuda.synchronize()
-            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            ev[0].record(stream)
-            st = plans[guided].run(stream.cuda_stream)
-            ev[1].record(stream)
-            torch.cuda.synchronize()
-            return ev[0].elapsed_time(ev[1]), st["walk_steps"]
-    for i in range(args.warmup):
-        solve(i)
-    ms, steps = 0.0, 0
-    for i in range(args.steps):
-        t, n = solve(100 + i)
-        ms += t
-        steps += n
-    pms, psteps = solve(999, guided=False)
-    line = {"metric": METRIC, "value": steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 geometry, bf16 MLP, f64 accumulators", "data": "synthetic",
-            "config": dict(W, **extra), "plain_walk_steps_per_s": psteps / (pms / 1000.0)}
+    lo, hi = F.desc.lo[:WORKLOADS[key]["dim"]], F.desc.hi[:WORKLOADS[key]["dim"]]
+    line["decode"] = decode_line(ctx, F, WORKLOADS[key]["dim"], list(lo), list(hi))
+    line["l2_copy_gbs"] = ctx.l2_gbs
+    if not args.no_extras and key == HEADLINE:
+        extras = {}
+        xargs = argparse.Namespace(**vars(args))
+        xargs.cpu_seconds = min(args.cpu_seconds, 6.0)
+        for k in ("star2d", "sphere3d"):
+            l, _ = guided_rounds_line(ctx, k, xargs, full=True)
+            extras[k] = {x: l[x] for x in ("value", "unit", "steps", "warmup", "ms_per_step", "config", "clocks",
+                                           "gpu_launches", "e2e", "roofline", "cpu_baseline", "breakdown",
+                                           "plain_walk_steps_per_s", "relmse")}
+        extras["batch64"] = batch_line(ctx, xargs)
+        line["extras"] = extras
     print(json.dumps(line), flush=True)
     return 0
 
@@ -572,51 +634,45 @@ def run_once(args):
     import wost_inputs as wi
     from paper_2410_18944_gb300 import api, build
     build.build()
-    dim = 2
-    if args.workload == "sphere3d":
-        sc, pts = wi.config_3d_guided(res=WORKLOADS["sphere3d"]["grid"])
-        dim = 3
-    elif args.workload == "genus3":
-        sc, pts = wi.config_genus3(res=WORKLOADS["genus3"]["grid"])
-        dim = 3
-    else:
-        sc, pts = make_workload()
+    key = args.workload if args.workload in ("genus3", "sphere3d", "star2d") else HEADLINE
+    W = WORKLOADS[key]
+    sc, pts = make_workload(key)
     if args.points and args.points < len(pts):
         pts = wi.subsample(pts, args.points, seed=1)
     S = api.Scene(sc)
     lo, hi = S.bbox()
-    F = api.Field(dim, lo, hi)
+    F = api.Field(W["dim"], lo, hi)
     p = torch.tensor(pts, dtype=torch.float64, device="cuda")
     guided = args.once == "guided"
-    ts = WORKLOADS.get(args.workload, {}).get("train_samples", 0)
+    spp = args.spp or W.get("spp", 1)
     for rep in range(2):
-        m, v, st = api.solve(S, p, args.spp, eps=WORKLOAD["eps"], maxsteps=WORKLOAD["maxsteps"], seed=rep,
-                             guided=guided, field=F if guided else None, train=1 if guided else 0,
-                             train_samples=ts if guided else 0)
+        m, v, st = api.solve(S, p, spp, eps=W["eps"], maxsteps=W["maxsteps"], seed=rep, guided=guided,
+                             field=F if guided else None, train=1 if guided else 0,
+                             train_samples=W["train_samples"] if guided else 0)
         torch.cuda.synchronize()
         print(json.dumps({"once": args.once, "rep": rep, **{k: st[k] for k in (
-            "walk_steps", "ms_walk", "ms_train", "node_visits", "prim_visits", "kernel_launches", "records")}}))
+            "walk_steps", "ms_walk", "ms_train", "node_visits", "prim_visits", "kernel_launches", "records",
+            "walk_launches")}}))
     return 0
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["star2d", *WORKLOADS], default="star2d",
-                    help="star2d (the benchmark line) or another workload of the method")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default=HEADLINE,
+                    help="genus3 (the benchmark line) or another workload of the method as the main line")
     ap.add_argument("--once", choices=["plain", "guided"], default=None,
                     help="run one solve of the workload (profiling), no timing")
     ap.add_argument("--points", type=int, default=0, help="with --once: seeded subset of the query points")
-    ap.add_argument("--spp", type=int, default=WORKLOAD["spp"], help="with --once: walks per point")
+    ap.add_argument("--spp", type=int, default=0, help="with --once: walks per point (default: the workload's)")
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-relmse", action="store_true", help="skip the equal-time relMSE measurement")
-    ap.add_argument("--traffic", type=float, default=None,
-                    help="dram bytes per launch of the guided walk kernel from an ncu capture")
+    ap.add_argument("--no-extras", action="store_true", help="the main line only")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -624,8 +680,6 @@ def main():
         return run_once(args)
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload != "star2d":
-        return run_workload(args)
     return run_ours(args)
 
 
