@@ -651,8 +651,8 @@ def run_once(args):
                              train_samples=W["train_samples"] if guided else 0)
         torch.cuda.synchronize()
         print(json.dumps({"once": args.once, "rep": rep, **{k: st[k] for k in (
-            "walk_steps", "ms_walk", "ms_train", "node_visits", "prim_visits", "kernel_launches", "records",
-            "walk_launches")}}))
+            "walk_steps", "ms_walk", "ms_train", "node_visits", "prim_visits", "dir_prim_visits", "sil_prim_visits",
+            "neu_prim_visits", "kernel_launches", "records", "walk_launches")}}))
     return 0
 
 

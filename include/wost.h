@@ -175,6 +175,9 @@ typedef struct {
     double alg_bytes;          /* algorithmic bytes of the walk kernels: visited BVH nodes and
                                   primitives, hash-grid corner reads, query points, FP64
                                   accumulator updates, training-record writes and suffix pass */
+    int64_t dir_prim_visits;   /* of prim_visits: Dirichlet primitives (closest point) */
+    int64_t sil_prim_visits;   /* silhouette elements (closest silhouette) */
+    int64_t neu_prim_visits;   /* Neumann primitives (ray casts and the Neumann-flux sample) */
 } wost_stats;
 
 const char *wost_last_error(void);

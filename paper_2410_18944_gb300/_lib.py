@@ -55,7 +55,8 @@ class Stats(C.Structure):
                 ("records", C.c_int64), ("records_dropped", C.c_int64), ("train_steps", C.c_int32),
                 ("last_loss", C.c_float), ("ms_walk", C.c_double), ("ms_train", C.c_double),
                 ("kernel_launches", C.c_int64), ("walk_launches", C.c_int64), ("node_visits", C.c_int64),
-                ("prim_visits", C.c_int64), ("alg_bytes", C.c_double)]
+                ("prim_visits", C.c_int64), ("alg_bytes", C.c_double), ("dir_prim_visits", C.c_int64),
+                ("sil_prim_visits", C.c_int64), ("neu_prim_visits", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

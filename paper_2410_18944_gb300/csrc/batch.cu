@@ -480,6 +480,9 @@ extern "C" wost_status wost_batch_run(wost_batch *p, void *stream, wost_stats *s
         stats->walks = (int64_t)hs[2];
         stats->node_visits = (int64_t)hs[3];
         stats->prim_visits = (int64_t)(hs[4] + hs[5] + hs[6]);
+        stats->dir_prim_visits = (int64_t)hs[4];
+        stats->sil_prim_visits = (int64_t)hs[5];
+        stats->neu_prim_visits = (int64_t)hs[6];
         stats->records = (int64_t)hs[kCtrRec - kCtrStat];
         stats->records_dropped = (int64_t)hs[kCtrRec + 1 - kCtrStat];
         stats->train_steps = p->info.train_steps;

@@ -325,6 +325,9 @@ extern "C" wost_status wost_solve(wost_scene *s, wost_field *field, const double
         stats->walks = (int64_t)hs[2];
         stats->node_visits = (int64_t)hs[3];
         stats->prim_visits = (int64_t)(hs[4] + hs[5] + hs[6]);
+        stats->dir_prim_visits = (int64_t)hs[4];
+        stats->sil_prim_visits = (int64_t)hs[5];
+        stats->neu_prim_visits = (int64_t)hs[6];
         stats->alg_bytes = walk_alg_bytes(D, guided, hs, stats->records);
         stats->ms_walk = CallTiming::sum(tm.walk);
         stats->ms_train = CallTiming::sum(tm.train);
