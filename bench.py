@@ -76,6 +76,13 @@ WORKLOADS = {
                    dim=2, grid=512, spp=32, eps=1e-3, maxsteps=128, train_samples=1 << 18, subset=0,
                    ref_factor=16, step="one training round: one walk per point + its Adam steps",
                    l2="flushed (512 MiB write) before each step"),
+    "ablations": dict(workload="ablations of Sec. 6.2-6.3 and Tab. mis: on the 81,920-triangle icosphere (64 "
+                               "walks/point, minibatch training) the MIS modes (uniform only c = 0, fixed c = 0.5, "
+                               "guiding only c = 1, learned c), sample reflection off, and K = 4 against 8 lobes; on "
+                               "the 4096-segment star (512 walks/point) the training budget train_until_wpp in "
+                               "{64, 128, 256, 512}; relMSE on the icosphere's 4096-point subset / the star's grid",
+                      dim=3, eps=1e-3, maxsteps=128, step="one full solve per variant",
+                      l2="flushed (512 MiB write) before each solve"),
     "batch64": dict(workload="64 independent 2D star scenes (256-16384 segments log-uniform, Neumann fraction "
                              "U(0.2, 0.5), 1k-256k points and 8-128 walks per point log-uniform), one persistent "
                              "launch per training round under a CUDA graph, guided with online training per scene "
@@ -587,6 +594,64 @@ def batch_line(ctx, args):
     return line
 
 
+def ablation_line(ctx, args):
+    """relMSE of guided variants at equal walks and at equal time (the
+    plain solve's time per walk measured alongside)."""
+    torch, api, wi = ctx.torch, ctx.api, ctx.wi
+    out = {}
+
+    def variants(key, specs, spp, subset, ref_factor):
+        W = WORKLOADS[key]
+        sc, pts_np = make_workload(key)
+        S = api.Scene(sc)
+        lo, hi = S.bbox()
+        pts = torch.tensor(pts_np, dtype=torch.float64, device=ctx.dev)
+        npts = len(pts_np)
+        sub = (np.sort(np.random.default_rng(7).choice(npts, subset, replace=False)) if subset and subset < npts
+               else np.arange(npts))
+        sub_t = torch.tensor(sub, device=ctx.dev)
+        psub = pts[sub_t].contiguous()
+        common = dict(eps=W["eps"], maxsteps=W["maxsteps"], stream=ctx.stream)
+        ref, rvar, _ = api.solve(S, psub, spp * ref_factor, seed=424242, **common)
+        ref, rvar = ref.cpu().numpy(), rvar.cpu().numpy()
+
+        def rel(u):   # the reference's own variance removed
+            return float(np.mean(((u - ref) ** 2 - rvar) / (ref ** 2 + 1e-2)))
+        nplain = min(spp, max(2, -(-(1 << 22) // npts)))
+        pms, (mp, _, stp) = ctx.timed(lambda: api.solve(S, pts, nplain, seed=92, **common), flush=True)
+        plain_s_per_walk = pms / 1000.0 / nplain
+        m_sp = api.solve(S, psub, spp, seed=616161, **common)[0].cpu().numpy()
+        res = {"plain": {"relmse_equal_spp": rel(m_sp), "s_per_solve": plain_s_per_walk * spp}}
+        for name, fkw, ekw in specs:
+            F = api.Field(W["dim"], lo, hi, seed=1, **fkw)
+            ms, (m, v, st) = ctx.timed(lambda: api.solve(S, pts, spp, seed=77, guided=True, field=F, train=1,
+                                                         train_samples=W.get("train_samples", 0), **common,
+                                                         **ekw), flush=True)
+            g_s = ms / 1000.0
+            spp_eq = max(1, int(spp * g_s / (plain_s_per_walk * spp)))
+            m_eq = api.solve(S, psub, spp_eq, seed=515151, **common)[0].cpu().numpy()
+            rg = rel(m.cpu().numpy()[sub])
+            res[name] = {"relmse_equal_spp": rg, "s_per_solve": g_s, "walk_steps_per_s": st["walk_steps"] / g_s,
+                         "plain_spp_at_equal_time": spp_eq, "plain_relmse_equal_time": rel(m_eq),
+                         "equal_time_ratio_plain_over_guided": rel(m_eq) / rg,
+                         "variance_reduction_equal_spp": res["plain"]["relmse_equal_spp"] / rg}
+            print(json.dumps({"ablation": key, "variant": name, **res[name]}), flush=True)
+        return res
+
+    out["icosphere_64wpp"] = variants("sphere3d", [
+        ("learned c (default)", {}, {}),
+        ("fixed c = 0.5", {}, dict(c_mode=1, c_fixed=0.5)),
+        ("guiding only, c = 1", {}, dict(c_mode=1, c_fixed=1.0)),
+        ("uniform only, c = 0", {}, dict(c_mode=1, c_fixed=0.0)),
+        ("no sample reflection", {}, dict(reflect=0)),
+        ("K = 4 lobes", dict(K=4), {}),
+    ], 64, 4096, 32)
+    out["star_512wpp_training_budget"] = variants("star2d", [
+        (f"train_until_wpp = {b}", {}, dict(train_until_wpp=b)) for b in (64, 128, 256, 512)
+    ], 512, 0, 4)
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = env_rank()
@@ -604,6 +669,12 @@ def run_ours(args):
         dist.barrier()
     ctx = Ctx(torch, api, wi, dev)
     ctx.l2_gbs = measure_l2_copy_gbs(ctx)
+    if args.workload == "ablations":
+        if rank == 0:
+            res = ablation_line(ctx, args)
+            print(json.dumps({"metric": METRIC, "unit": UNIT, "impl": "ours",
+                              "config": dict(WORKLOADS["ablations"]), "ablations": res}), flush=True)
+        return 0
     key = args.workload if args.workload in ("genus3", "sphere3d", "star2d") else HEADLINE
     line, F = guided_rounds_line(ctx, key, args, rank, world, full=True)
     if rank != 0:
