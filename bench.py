@@ -23,7 +23,10 @@ whole job over all ranks.  The line also carries the equal-time relMSE of
 guided vs plain WoSt on a seeded 4096-point subset, and extra lines for the
 2D star (4096 segments, 512 x 512 grid, 32 walks/point), the 81,920-triangle
 icosphere with Gaussian sources (256 x 256 slice, 64 walks/point) and 64
-uneven 2D scenes in one persistent launch per round under a CUDA graph.
+uneven 2D scenes in one persistent launch per round under a CUDA graph.  The
+star and the icosphere have far fewer points than the slice, so their
+training batches hold 4 and 8 walks per point (696k and 376k walks; the
+sizes measured best at equal time) and a step of theirs is one such batch.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -56,29 +59,35 @@ WORKLOADS = {
     "genus3": dict(workload="3D mixed Dirichlet/Neumann Laplace guided WoSt with learned MIS selection: genus-3 "
                             "solid (sphere displaced by 0.15 Perlin noise minus three smoothly rimmed tunnels, "
                             "993,640 triangles by surface nets), 30% Neumann cap, g = 1/|x - c|, 1024x1024 slice "
-                            "z = 0 masked inside, 128 walks/point, online training after every batch in minibatches "
+                            "z = 0 masked inside, 128 walks/point, online training after every batch of one walk per point in minibatches "
                             "of 2^18 records, 16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 MLP, K = 8",
                    dim=3, grid=1024, spp=128, eps=1e-3, maxsteps=128, train_samples=1 << 18, subset=4096,
-                   ref_factor=64, step="one training round: one walk per point of the slice + its Adam steps",
+                   ref_factor=64, batch_wpp=1,
+                   step="one training batch: one walk per point of the slice (510k walks) + its Adam steps",
                    l2="inputs larger than L2 (about 300 MB of BVH, 510k-walk batches); no flush"),
     "sphere3d": dict(workload="3D mixed Dirichlet/Neumann Poisson guided WoSt: icosphere 81,920 triangles displaced "
                               "by 0.15 Perlin noise, 30% Neumann cap, f = 4 Gaussians (sigma 0.1), g = 1/|x - c|, "
                               "256x256 slice z = 0 masked inside, 64 walks/point, online training after every batch "
-                              "in minibatches of 2^18 records, 16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 "
+                              "of 8 walks per point in minibatches of 2^18 records, 16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 "
                               "MLP, K = 8",
                      dim=3, grid=256, spp=64, eps=1e-3, maxsteps=128, train_samples=1 << 18, subset=4096,
-                     ref_factor=64, step="one training round: one walk per point + its Adam steps",
+                     ref_factor=64, batch_wpp=8,
+                     step="one training batch: 8 walks per point (376k walks) + its Adam steps",
                      l2="flushed (512 MiB write) before each step"),
     "star2d": dict(workload="2D mixed Dirichlet/Neumann guided WoSt: star polyline 4096 segments, 40% zero-flux "
                             "Neumann arc, g = x^2 - y^2, 512x512 grid masked inside, 32 walks/point, online training "
-                            "after every batch in minibatches of 2^18 records, 16-level 2^16-entry FP16 hash grid + "
+                            "after every batch of 4 walks per point in minibatches of 2^18 records, 16-level 2^16-entry FP16 hash grid + "
                             "32-64-64-33 BF16 MLP, K = 8",
                    dim=2, grid=512, spp=32, eps=1e-3, maxsteps=128, train_samples=1 << 18, subset=0,
-                   ref_factor=16, step="one training round: one walk per point + its Adam steps",
+                   ref_factor=16, batch_wpp=4,
+                   step="one training batch: 4 walks per point (696k walks) + its Adam steps",
                    l2="flushed (512 MiB write) before each step"),
     "ablations": dict(workload="ablations of Sec. 6.2-6.3 and Tab. mis: on the 81,920-triangle icosphere (64 "
-                               "walks/point, minibatch training) the MIS modes (uniform only c = 0, fixed c = 0.5, "
-                               "guiding only c = 1, learned c), sample reflection off, and K = 4 against 8 lobes; on "
+                               "walks/point, training batches of 8 walks/point in minibatches) the MIS modes "
+                               "(uniform only c = 0, fixed c = 0.5, guiding only c = 1, learned c), sample "
+                               "reflection off, K = 4 against 8 lobes, and training batches of 1, 4 and 16 "
+                               "walks/point; "
+                               "on "
                                "the 4096-segment star (512 walks/point) the training budget train_until_wpp in "
                                "{64, 128, 256, 512}; relMSE on the icosphere's 4096-point subset / the star's grid",
                       dim=3, eps=1e-3, maxsteps=128, step="one full solve per variant",
@@ -395,13 +404,20 @@ def guided_rounds_line(ctx, key, args, rank=0, world=1, full=True):
     sub_t = torch.tensor(sub, device=ctx.dev)
     acc = torch.zeros(nsub, dtype=torch.float64, device=ctx.dev)
 
+    # a step is one training batch of B walks per point (Sec. 5.2 trains
+    # after batches of one walk per point of a 1024^2 grid, about 2^20
+    # walks; the smaller point sets take B walks per point per batch)
+    B = W.get("batch_wpp", 1)
+    nbatch = spp // B
+    assert nbatch * B == spp
+
     def round_(r):
-        ms, (m, v, st) = ctx.timed(lambda: api.solve(S, pts, 1, walk_begin=r, **gkw), flush=flush)
-        acc.add_(m[sub_t])
+        ms, (m, v, st) = ctx.timed(lambda: api.solve(S, pts, B, walk_begin=r * B, batch_wpp=B, **gkw), flush=flush)
+        acc.add_(m[sub_t], alpha=B)
         return ms, st
 
-    warm = min(args.warmup, spp - 1)
-    nsteps = max(1, min(args.steps, spp - warm))
+    warm = min(args.warmup, nbatch - 1)
+    nsteps = max(1, min(args.steps, nbatch - warm))
     for r in range(warm):
         round_(r)
     if world > 1:
@@ -426,9 +442,11 @@ def guided_rounds_line(ctx, key, args, rank=0, world=1, full=True):
     if not full or rank != 0:
         return line, None
     # the rest of the solve (untimed): every round of the spp-walk estimate
-    for r in range(warm + nsteps, spp):
-        round_(r)
-    guided_s = (sum(per_ms) / nsteps) * spp / 1000.0     # a full solve at the timed rate
+    # (only the relMSE needs it)
+    if not args.no_relmse:
+        for r in range(warm + nsteps, nbatch):
+            round_(r)
+    guided_s = (sum(per_ms) / nsteps) * nbatch / 1000.0  # a full solve at the timed rate
     # plain walks: time per walk over the whole point set, in one launch of
     # at least 4 M walks (as a plain solve would run them) or all spp walks
     nplain = min(spp, max(2, -(-(1 << 22) // npts)))
@@ -437,7 +455,7 @@ def guided_rounds_line(ctx, key, args, rank=0, world=1, full=True):
     plain_rate = stp["walk_steps"] / (pms / 1000.0)
     plain_s = pms / 1000.0 * spp / nplain                 # a full plain solve at spp walks
     psub = pts[sub_t].contiguous()
-    guided_mean = (acc / spp).cpu().numpy()
+    guided_mean = (acc / (B * (warm + nsteps) if args.no_relmse else spp)).cpu().numpy()
     relmse = None
     if not args.no_relmse:
         spp_ref = W["ref_factor"] * spp
@@ -468,13 +486,14 @@ def guided_rounds_line(ctx, key, args, rank=0, world=1, full=True):
     pts_host = torch.tensor(pts_np, dtype=torch.float64).pin_memory().numpy()
     F.set_params(init["grid"], init["W1"], init["W2"], init["W3"], init["b3"])
     e2e_steps, e2e_s = 0, 0.0
-    for r in range(3):
+    for r in range(min(3, nbatch)):
         if flush:
             ctx.flush()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        m, v, st = api.solve(S, pts_host, 1, walk_begin=r, guided=True, field=F, train=1, train_until_wpp=256,
-                             train_samples=W["train_samples"], seed=seed + 1, eps=W["eps"], maxsteps=W["maxsteps"])
+        m, v, st = api.solve(S, pts_host, B, walk_begin=r * B, guided=True, field=F, train=1, train_until_wpp=256,
+                             batch_wpp=B, train_samples=W["train_samples"], seed=seed + 1, eps=W["eps"],
+                             maxsteps=W["maxsteps"])
         e2e_s += time.perf_counter() - t0
         e2e_steps += st["walk_steps"]
     line["e2e"] = {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(npts * dim * 8),
@@ -624,6 +643,7 @@ def ablation_line(ctx, args):
         res = {"plain": {"relmse_equal_spp": rel(m_sp), "s_per_solve": plain_s_per_walk * spp}}
         for name, fkw, ekw in specs:
             F = api.Field(W["dim"], lo, hi, seed=1, **fkw)
+            ekw = {"batch_wpp": W.get("batch_wpp", 1), **ekw}
             ms, (m, v, st) = ctx.timed(lambda: api.solve(S, pts, spp, seed=77, guided=True, field=F, train=1,
                                                          train_samples=W.get("train_samples", 0), **common,
                                                          **ekw), flush=True)
@@ -645,6 +665,9 @@ def ablation_line(ctx, args):
         ("uniform only, c = 0", {}, dict(c_mode=1, c_fixed=0.0)),
         ("no sample reflection", {}, dict(reflect=0)),
         ("K = 4 lobes", dict(K=4), {}),
+        ("training batch of 1 walk/point", {}, dict(batch_wpp=1)),
+        ("training batch of 4 walks/point", {}, dict(batch_wpp=4)),
+        ("training batch of 16 walks/point", {}, dict(batch_wpp=16)),
     ], 64, 4096, 32)
     out["star_512wpp_training_budget"] = variants("star2d", [
         (f"train_until_wpp = {b}", {}, dict(train_until_wpp=b)) for b in (64, 128, 256, 512)

@@ -156,6 +156,15 @@ typedef struct {
                                   one warp on others (a decode tile filled, decoded or consumed);
                                   0 = 2 s.  A wait that runs out ends the launch and the call
                                   returns WOST_ERR_TIMEOUT; the device stays usable */
+    int32_t batch_wpp;         /* wost_solve, guided with train: walks per point in one training
+                                  batch (Sec. 5.2: a batch is one walk per point of a 1024^2 grid,
+                                  about 2^20 walks; a smaller point set takes several walks per
+                                  point to fill a batch of that size).  0 or 1 = one walk per
+                                  point.  Batch b holds walks [w0 + b B, w0 + (b + 1) B) of every
+                                  point (B = batch_wpp, the last batch clipped at train_until_wpp
+                                  and nwalks); the field trains after each batch on all its
+                                  records; the walks past train_until_wpp are not batched.  The
+                                  random numbers of a walk do not depend on the grouping */
 } wost_exec;
 
 typedef struct {
@@ -203,8 +212,9 @@ wost_status wost_scene_bbox(const wost_scene *scene, double lo[3], double hi[3])
    domain get NaN, points inside the eps-shell get g at the closest Dirichlet
    point with variance 0.  out_mean[i] is the sample mean, out_var[i]
    (nullable) the variance of that mean.  guided != 0 requires a field; with
-   exec->train the field is trained after every batch of one walk per point
-   (Sec. 5.2) until train_until_wpp walks per point.  Batches run in order,
+   exec->train the field is trained after every batch of exec->batch_wpp
+   walks per point (one by default, Sec. 5.2) until train_until_wpp walks per
+   point.  Batches run in order,
    so the estimate is deterministic up to floating-point atomics. */
 wost_status wost_solve(wost_scene *scene, wost_field *field, const double *points,
                        int64_t npoints, int32_t nwalks, double eps, int32_t maxsteps,
@@ -378,7 +388,7 @@ wost_status wost_solve_batch(int32_t njobs, const wost_job *jobs, int32_t guided
    The scene must belong to the current device (WOST_ERR_INVALID_ARG
    otherwise, before any launch).
    The first call on a device looks up the array's device address with
-   cudaGetSymbolAddress (make it before any stream capture).  Every call
+   cudaGetSymbolAddress.  Every call
    reuses the same array and clears what must start at zero; calls whose GPU
    work overlaps (e.g. issued on two streams) race on it. */
 #define WOST_STATIC_MAX_POINTS 262144

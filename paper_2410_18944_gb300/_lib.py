@@ -47,7 +47,7 @@ class Exec(C.Structure):
                 ("max_train_records", C.c_int64), ("walk_begin", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("guided_kernel", C.c_int32), ("wavefront_slots", C.c_int32),
                 ("train_samples", C.c_int64), ("rr_depth", C.c_int32), ("rr_survival", C.c_float),
-                ("wait_ns", C.c_int64)]
+                ("wait_ns", C.c_int64), ("batch_wpp", C.c_int32)]
 
 
 class Stats(C.Structure):

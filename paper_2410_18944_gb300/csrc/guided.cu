@@ -21,8 +21,26 @@ struct GuidedArgs {
     int stage_mask;    // scene regions staged in shared memory (stage_plan)
 };
 
-template <int D>
-__global__ void __launch_bounds__(kWsThreads, 1) guided_walk_kernel(const __grid_constant__ GuidedArgs g) {
+// Walker warps of the single-scene kernel: kWsWalkerWarps (12) when the
+// scene's traversal data (BVH nodes, cones, primitives) fits comfortably in
+// L2 or shared memory, kWsWalkersWide beside the 4 servers when it does not.
+// Measured on one GB300, one recording round: genus-3 solid (about 300 MB of
+// traversal data) 1057 ms with 12 walker warps, 964 with 14, 798 with 20,
+// 729 with 24, 695 with 28 (32 warps, the 1024-thread limit); icosphere of
+// 82k triangles (about 20 MB) 168, 172, 174 ms with 12, 14, 20.  More
+// walkers hide the latency of BVH loads that miss L2; with the scene in L2
+// the register cap they impose (64 per thread at 1024 threads, with spills)
+// costs more than it hides.
+#ifndef WOST_WS_WALKERS_WIDE
+#define WOST_WS_WALKERS_WIDE 28
+#endif
+constexpr int kWsWalkersWide = WOST_WS_WALKERS_WIDE;
+#ifndef WOST_WS_WIDE_MB
+#define WOST_WS_WIDE_MB 64
+#endif
+
+template <int D, int W>
+__global__ void __launch_bounds__(ws_threads(W), 1) guided_walk_kernel(const __grid_constant__ GuidedArgs g) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ DevScene staged;
     const DevScene *sc = &g.w.sc;
@@ -30,7 +48,21 @@ __global__ void __launch_bounds__(kWsThreads, 1) guided_walk_kernel(const __grid
         stage_scene(g.w.sc, staged, reinterpret_cast<float4 *>(sm + kWsSmem), g.stage_mask);
         sc = &staged;
     }
-    guided_ws_body<D, false>(SoloSrc<D>{g.w, &g.f, g.rd, sc}, g.o, sm);
+    guided_ws_body<D, false, W>(SoloSrc<D>{g.w, &g.f, g.rd, sc}, g.o, sm);
+}
+
+// bytes of the scene's traversal data (the three BVHs' nodes and primitives
+// and the silhouette cones)
+static size_t traversal_bytes(const DevScene &s) {
+    const size_t nb = 16 * (size_t)(s.dim == 2 ? node_f4<2>() : node_f4<3>());
+    const size_t pd = s.dim == 2 ? 16 : 48, ps = s.dim == 2 ? 32 : 64;
+    return nb * ((size_t)s.dir.nnodes + s.neu.nnodes + s.sil.nnodes) + pd * ((size_t)s.dir.nprims + s.neu.nprims) +
+           ps * (size_t)s.sil.nprims + 16 * (size_t)bvh_width(s.dim) * s.sil.nnodes;
+}
+
+// the walker-warp count of a scene's guided launches
+static int ws_walkers_for(const DevScene &s) {
+    return traversal_bytes(s) > ((size_t)WOST_WS_WIDE_MB << 20) ? kWsWalkersWide : kWsWalkerWarps;
 }
 
 // decode of arbitrary points: the same tile forward as inside the walk
@@ -117,12 +149,16 @@ static int stage_budget_bytes() {
     if (budget < 0) {
         int dev = 0, optin = 0;
         cudaFuncAttributes f2{}, f3{};
+        cudaFuncAttributes w2{}, w3{};
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-            cudaFuncGetAttributes(&f2, guided_walk_kernel<2>) != cudaSuccess ||
-            cudaFuncGetAttributes(&f3, guided_walk_kernel<3>) != cudaSuccess)
+            cudaFuncGetAttributes(&f2, guided_walk_kernel<2, kWsWalkerWarps>) != cudaSuccess ||
+            cudaFuncGetAttributes(&f3, guided_walk_kernel<3, kWsWalkerWarps>) != cudaSuccess ||
+            cudaFuncGetAttributes(&w2, guided_walk_kernel<2, kWsWalkersWide>) != cudaSuccess ||
+            cudaFuncGetAttributes(&w3, guided_walk_kernel<3, kWsWalkersWide>) != cudaSuccess)
             return 0;
-        const int stat = (int)std::max(f2.sharedSizeBytes, f3.sharedSizeBytes);
+        const int stat = (int)std::max(std::max(f2.sharedSizeBytes, f3.sharedSizeBytes),
+                                       std::max(w2.sharedSizeBytes, w3.sharedSizeBytes));
         budget = std::max(0, std::min(optin - kWsSmem - stat - 1024, WOST_STAGE_MAX_KB * 1024));
     }
     return budget;
@@ -132,8 +168,14 @@ wost_status guided_occupancy(int dim, int *per_sm) {
     static bool set[4] = {false, false, false, false};
     if (!set[dim]) {
         const int bytes = kWsSmem + stage_budget_bytes();
-        if (dim == 2) WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-        else WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if (dim == 2) {
+            WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<2, kWsWalkerWarps>, at, bytes));
+            WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<2, kWsWalkersWide>, at, bytes));
+        } else {
+            WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<3, kWsWalkerWarps>, at, bytes));
+            WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<3, kWsWalkersWide>, at, bytes));
+        }
         set[dim] = true;
     }
     *per_sm = 1;
@@ -149,8 +191,12 @@ wost_status launch_guided(int dim, const GuidedArgs &g, int grid, cudaStream_t s
     int f4 = 0;
     stage_mask_for(g.w.sc, &f4);
     const int smem = kWsSmem + f4 * 16;
-    if (dim == 2) guided_walk_kernel<2><<<grid, kWsThreads, smem, st>>>(g);
-    else guided_walk_kernel<3><<<grid, kWsThreads, smem, st>>>(g);
+    const bool wide = ws_walkers_for(g.w.sc) == kWsWalkersWide;
+    constexpr int tn = ws_threads(kWsWalkerWarps), tw = ws_threads(kWsWalkersWide);
+    if (dim == 2 && wide) guided_walk_kernel<2, kWsWalkersWide><<<grid, tw, smem, st>>>(g);
+    else if (dim == 2) guided_walk_kernel<2, kWsWalkerWarps><<<grid, tn, smem, st>>>(g);
+    else if (wide) guided_walk_kernel<3, kWsWalkersWide><<<grid, tw, smem, st>>>(g);
+    else guided_walk_kernel<3, kWsWalkerWarps><<<grid, tn, smem, st>>>(g);
     WOST_CUDA(cudaGetLastError());
     return WOST_OK;
 }
@@ -191,15 +237,18 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
     const int rounds = ex.train ? std::max(0, std::min(nwalks, ex.train_until_wpp - walk_begin)) : 0;
     const bool wavefront = ex.guided_kernel == 2 || (ex.guided_kernel == 0 && rounds == 0);
     const bool ws_then_wavefront = ex.guided_kernel == 0 && rounds > 0 && rounds < nwalks;
+    // walks per point in one training batch (the last one clipped at `rounds`)
+    const int bwpp = std::max(1, std::min(ex.batch_wpp, std::max(rounds, 1)));
     int ntrain = 0;
-    // one wavefront launch of `items` walks from walk index w0
-    auto run_wavefront = [&](int w0, unsigned long long items, bool record) -> wost_status {
+    // one wavefront launch of `items` walks from walk index w0; a recording
+    // launch appends to the batch's records (`fresh`: the batch's first)
+    auto run_wavefront = [&](int w0, unsigned long long items, bool record, bool fresh) -> wost_status {
         WalkArgs w = a;
         w.walk_begin = w0;
         w.total = items;
         g.o.record = record;
         WOST_CUDA(cudaMemsetAsync(a.work_ctr, 0, sizeof(unsigned long long), st));
-        if (record) WOST_CUDA(cudaMemsetAsync(f->rec_ctr, 0, 2 * sizeof(unsigned long long), st));
+        if (record && fresh) WOST_CUDA(cudaMemsetAsync(f->rec_ctr, 0, 2 * sizeof(unsigned long long), st));
         int64_t iters = 0;
         const int slots = record ? (int)a.npoints : (ex.wavefront_slots > 0 ? ex.wavefront_slots : kWfMaxSlots);
         tm.mark(tm.walk, st);
@@ -220,25 +269,32 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
     };
     g.rd = RecDest{f->rec, f->rec_ctr, f->rec_cap};
     g.o.scratch_steps = a.maxsteps;
+    // record buffer of one batch: 64 records per walk by default
+    const int64_t rec_cap = ex.max_train_records > 0 ? ex.max_train_records
+                                                     : std::max<int64_t>(a.npoints * 64 * bwpp, 1 << 20);
     if (wavefront) {
-        // one launch of npoints walks per training round, then every
-        // remaining walk in one launch (the random numbers of a walk do not
-        // depend on how walks are grouped into launches)
+        // a training batch of B walks per point is B recording launches of
+        // one walk per point (a recording launch holds one slot per walk),
+        // then the field trains on the batch's records; then every remaining
+        // walk in one launch (the random numbers of a walk do not depend on
+        // how walks are grouped into launches)
         if (rounds > 0) {
-            int64_t cap = ex.max_train_records > 0 ? ex.max_train_records : std::max<int64_t>(a.npoints * 64, 1 << 20);
             size_t scratch = (size_t)a.npoints * (size_t)std::max(a.maxsteps, 1) * kRecFloats * sizeof(float);
-            wost_status rc = ensure_records(f, cap, scratch);
+            wost_status rc = ensure_records(f, rec_cap, scratch);
             if (rc != WOST_OK) return rc;
             g.rd = RecDest{f->rec, f->rec_ctr, f->rec_cap};
         }
         g.o.scratch = f->scratch;
-        for (int b = 0; b < rounds; ++b) {
-            wost_status rc = run_wavefront(walk_begin + b, (unsigned long long)a.npoints, true);
+        for (int b = 0; b < rounds; b += bwpp) {
+            const int nb = std::min(bwpp, rounds - b);
+            wost_status rc = WOST_OK;
+            for (int j = 0; j < nb && rc == WOST_OK; ++j)
+                rc = run_wavefront(walk_begin + b + j, (unsigned long long)a.npoints, true, j == 0);
             if (rc == WOST_OK) rc = train_after();
             if (rc != WOST_OK) return rc;
         }
         if (rounds < nwalks) {
-            wost_status rc = run_wavefront(walk_begin + rounds, (unsigned long long)a.npoints * (nwalks - rounds), false);
+            wost_status rc = run_wavefront(walk_begin + rounds, (unsigned long long)a.npoints * (nwalks - rounds), false, false);
             if (rc != WOST_OK) return rc;
         }
     } else {
@@ -248,18 +304,22 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
         int cps = ex.ctas_per_sm > 0 ? std::min(ex.ctas_per_sm, occ) : occ;
         int grid = num_sms() * cps;
         if (rounds > 0) {
-            int64_t cap = ex.max_train_records > 0 ? ex.max_train_records : std::max<int64_t>(a.npoints * 64, 1 << 20);
-            size_t scratch = (size_t)grid * (kWsWalkerWarps * 32) * (size_t)std::max(a.maxsteps, 1) * kRecFloats * sizeof(float);
-            wost_status rc = ensure_records(f, cap, scratch);
+            size_t scratch = (size_t)grid * (ws_walkers_for(s->dev) * 32) * (size_t)std::max(a.maxsteps, 1) *
+                             kRecFloats * sizeof(float);
+            wost_status rc = ensure_records(f, rec_cap, scratch);
             if (rc != WOST_OK) return rc;
             g.rd = RecDest{f->rec, f->rec_ctr, f->rec_cap};
         }
         g.o.scratch = f->scratch;
         const int ws_walks = ws_then_wavefront ? rounds : nwalks;
-        for (int b = 0; b < ws_walks; ++b) {
+        // one launch per training batch (its scratch rows belong to walker
+        // lanes, so a launch may hold several walks per point), one launch
+        // per walk index after training
+        for (int b = 0, nb = 1; b < ws_walks; b += nb) {
+            nb = b < rounds ? std::min(bwpp, rounds - b) : 1;
             g.w = a;
             g.w.walk_begin = walk_begin + b;
-            g.w.total = (unsigned long long)a.npoints;
+            g.w.total = (unsigned long long)a.npoints * (unsigned long long)nb;
             g.o.record = b < rounds;
             WOST_CUDA(cudaMemsetAsync(a.work_ctr, 0, sizeof(unsigned long long), st));
             if (g.o.record) WOST_CUDA(cudaMemsetAsync(f->rec_ctr, 0, 2 * sizeof(unsigned long long), st));
@@ -272,7 +332,7 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
             if (g.o.record && (rc = train_after()) != WOST_OK) return rc;
         }
         if (ws_then_wavefront) {
-            wost_status rc = run_wavefront(walk_begin + rounds, (unsigned long long)a.npoints * (nwalks - rounds), false);
+            wost_status rc = run_wavefront(walk_begin + rounds, (unsigned long long)a.npoints * (nwalks - rounds), false, false);
             if (rc != WOST_OK) return rc;
         }
     }

@@ -56,7 +56,9 @@ constexpr int kWsServerWarps = 4;
 #define WOST_WS_TILES 1
 #endif
 constexpr int kWsWalkerWarps = WOST_WS_WALKERS;
-constexpr int kWsThreads = 32 * (kWsServerWarps + kWsWalkerWarps);
+// threads of a CTA with W walker warps beside the decode servers
+__host__ __device__ constexpr int ws_threads(int W) { return 32 * (kWsServerWarps + W); }
+constexpr int kWsThreads = ws_threads(kWsWalkerWarps);
 // decode tile buffers.  Measured on one GB300: one buffer is 6% faster than
 // two on the 2D star and 3-5% on the icosphere (equal on the genus-3 solid);
 // three and four are slower still.  A walker warp that finds the buffer busy
@@ -176,8 +178,11 @@ __device__ __forceinline__ void end_recorded_walk(const RecDest &rd, const float
     }
 }
 
-template <int D, bool kMulti, class Src>
+// W walker warps (a template parameter: launches over scenes whose traversal
+// data misses L2 take more walkers to hide its latency)
+template <int D, bool kMulti, int W = kWsWalkerWarps, class Src>
 __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, uint8_t *sm) {
+    constexpr int kThreads = ws_threads(W);
     constexpr int kSlots = ws_weight_slots(kMulti);
     uint8_t *wslots = sm;
     uint8_t *bufs = sm + kSlots * kWImgBytes;
@@ -194,7 +199,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
     };
 
     if (!kMulti)
-        for (int i = tid; i < kWImgBytes / 16; i += kWsThreads)
+        for (int i = tid; i < kWImgBytes / 16; i += kThreads)
             reinterpret_cast<uint4 *>(wslots)[i] = __ldg(src.wimg(0) + i);
     if (tid == 0) {
         for (int b = 0; b < kNT; ++b) {
@@ -204,7 +209,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
         }
         mbar_init(&ctl->mma, 1);
         ctl->qclaim = 0;
-        ctl->alive = kWsWalkerWarps;
+        ctl->alive = W;
         ctl->wnext = 0;
         for (int i = 0; i < kWSlots; ++i) ctl->wtag[i] = -1;
         fence_mbar_init();
@@ -374,7 +379,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
         }
     } else {
         // ------------------------------ walkers -----------------------------
-        const int slot = blockIdx.x * (kWsWalkerWarps * 32) + (tid - 32 * kWsServerWarps);
+        const int slot = blockIdx.x * (W * 32) + (tid - 32 * kWsServerWarps);
         float *scratch_row = o.scratch + (size_t)slot * o.scratch_steps * kRecFloats;
         const float area = D == 2 ? 2.f * WOST_PI : 4.f * WOST_PI;
         Walk<D> w;

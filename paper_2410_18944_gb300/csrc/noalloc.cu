@@ -12,7 +12,7 @@
 //
 // Set-up: the device address of the array is looked up with
 // cudaGetSymbolAddress once per device, by the first call made while that
-// device is current; make that first call before any stream capture.
+// device is current.
 // All calls share the one array and it keeps the last call's contents; each
 // call clears what must start at zero.  Two calls whose work overlaps on the
 // GPU (e.g. on different streams) race on the array.

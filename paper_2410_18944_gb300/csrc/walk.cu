@@ -224,6 +224,7 @@ extern "C" wost_status wost_solve(wost_scene *s, wost_field *field, const double
         set_error("wost_solve: rr_depth must be >= 0 and rr_survival in (0, 1]");
         return WOST_ERR_INVALID_ARG;
     }
+    if (exec && exec->batch_wpp < 0) { set_error("wost_solve: batch_wpp must be >= 0"); return WOST_ERR_INVALID_ARG; }
     {
         wost_status dc = check_device(s->device, "wost_solve (scene)");
         if (dc == WOST_OK && guided) dc = check_device(field->device, "wost_solve (field)");

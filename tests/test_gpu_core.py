@@ -431,6 +431,47 @@ def test_online_training_runs_and_stays_unbiased(api):
     assert np.all(np.isfinite(p["W1"])) and np.all(np.isfinite(p["grid"]))
 
 
+def test_training_batches_of_several_walks_per_point(api):
+    # batch_wpp = B: the field trains after each batch of B walks per point
+    # (the last batch clipped at train_until_wpp), so every walk of the first
+    # batch uses the initial field: the estimate equals a frozen-field solve.
+    # The warp-specialised kernel runs a batch in one launch, the wavefront in
+    # B launches of one walk per point; both gather the same records.
+    sc = wi.half_disk(48, 12)
+    S = api.Scene(sc)
+    pts = _interior(sc, 256, 14)
+    lo, hi = S.bbox()
+    common = dict(eps=1e-3, maxsteps=256, seed=23, guided=True)
+    F0 = api.Field(2, lo, hi, seed=5)
+    m0, _, s0 = api.solve(S, pts, 4, field=F0, **common)
+    init = F0.get_params()
+    res = []
+    for kern in (1, 2):
+        F = api.Field(2, lo, hi, seed=5)
+        m, v, st = api.solve(S, pts, 4, field=F, train=1, train_until_wpp=4, batch_wpp=16, guided_kernel=kern,
+                             **common)
+        assert st["train_steps"] == 1 and st["walk_steps"] == s0["walk_steps"]
+        assert np.allclose(m, m0, rtol=1e-9, atol=1e-12)
+        res.append((st["records"], F.get_params()))
+    (r1, p1), (r2, p2) = res
+    assert r1 == r2 and r1 > 4 * 200
+    # one Adam step on the same records gathered in another order: equal up
+    # to the order of the gradient sums (a first Adam step moves an entry by
+    # about lr sign(g), so an entry whose sum cancels to rounding may differ)
+    for k in ("W1", "W3", "grid"):
+        assert not np.array_equal(p1[k], init[k])
+        assert np.mean(np.isclose(p1[k], p2[k], rtol=1e-3, atol=1e-6)) > 0.999, k
+    # batches of 16 and 8 walks per point, then 16 walks without training
+    F = api.Field(2, lo, hi, seed=5)
+    m, v, st = api.solve(S, pts, 40, field=F, train=1, train_until_wpp=24, batch_wpp=16, **common)
+    assert st["train_steps"] == 2 and st["walks"] == 40 * s0["walks"] // 4
+    ex = wi.eval_fn(sc.exact, pts)
+    z = (m - ex) / np.sqrt(v)
+    assert np.all(np.isfinite(m)) and np.mean(np.abs(z) < 4.0) > 0.98
+    with pytest.raises(Exception):
+        api.solve(S, pts, 2, field=F, train=1, batch_wpp=-1, **common)
+
+
 def test_guided_walks_stay_inside_star(api):
     # A walker that rounding leaves a hair outside a Neumann segment next to
     # a reflex vertex must not take the neighbouring segment's entry

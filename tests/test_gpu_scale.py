@@ -182,3 +182,23 @@ def test_genus3_mixed_vs_oracle_same_streams(api, genus3):
     # sample variance is too noisy to scale a z-score)
     zo = (mp - om) / np.sqrt(vp * (1 + 4096 / no))
     assert np.sum(zo ** 2) < 45 and np.all(np.abs(zo) < 5), zo
+
+
+def test_genus3_wide_walker_kernel_equals_wavefront(api, genus3):
+    # the genus-3 scene's traversal data misses L2, so its warp-specialised
+    # launches take the wide kernel (20 walker warps); with a frozen field it
+    # draws the same random numbers and decodes the same rows as the
+    # wavefront path: the same walks, estimates equal up to the order of the
+    # FP64 atomic sums
+    sc, pts = genus3
+    p = wi.subsample(pts, 3000, seed=6)
+    S = api.Scene(sc)
+    pd = torch.tensor(p, dtype=torch.float64, device="cuda")
+    F, _ = _random_field(api, 3, 10, sc, w_scale=1.0)
+    out = []
+    for kern in (1, 2):
+        m, v, st = api.solve(S, pd, 6, eps=1e-3, maxsteps=256, seed=41, guided=True, field=F, guided_kernel=kern)
+        out.append((m.cpu().numpy(), st))
+    (m1, s1), (m2, s2) = out
+    assert s1["walk_steps"] == s2["walk_steps"] and s1["walks"] == s2["walks"]
+    assert np.allclose(m1, m2, rtol=1e-9, atol=1e-12)
