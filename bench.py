@@ -742,7 +742,7 @@ def run_once(args):
     for rep in range(2):
         m, v, st = api.solve(S, p, spp, eps=W["eps"], maxsteps=W["maxsteps"], seed=rep, guided=guided,
                              field=F if guided else None, train=1 if guided else 0,
-                             train_samples=W["train_samples"] if guided else 0)
+                             train_samples=W["train_samples"] if guided else 0, batch_wpp=W.get("batch_wpp", 1))
         torch.cuda.synchronize()
         print(json.dumps({"once": args.once, "rep": rep, **{k: st[k] for k in (
             "walk_steps", "ms_walk", "ms_train", "node_visits", "prim_visits", "dir_prim_visits", "sil_prim_visits",
