@@ -165,6 +165,12 @@ typedef struct {
                                   and nwalks); the field trains after each batch on all its
                                   records; the walks past train_until_wpp are not batched.  The
                                   random numbers of a walk do not depend on the grouping */
+    int32_t walker_warps;      /* guided launches of the warp-specialised kernel: walker warps
+                                  per CTA beside its 4 decode-server warps, 0 (automatic), 12 or
+                                  28 (WOST_ERR_INVALID_ARG otherwise).  Automatic: wost_solve takes
+                                  28 when the scene's traversal data (BVH nodes, cones,
+                                  primitives) exceeds 64 MB, else 12; wost_batch_create lets its
+                                  autotuner choose.  Results do not depend on it */
 } wost_exec;
 
 typedef struct {
@@ -343,6 +349,7 @@ typedef struct {
     int32_t walk_launches;     /* walk launches in the graph (1, or 1 per training round + 1) */
     int32_t train_steps;       /* training steps in the graph */
     int64_t graph_nodes;
+    int32_t walker_warps;      /* guided walk launch: walker warps per CTA */
 } wost_batch_info;
 
 /* Plans a batch of njobs jobs, all of the same dimension: validates them,
@@ -355,7 +362,9 @@ typedef struct {
    record nothing and do not touch the fields.  guided != 0 needs a field
    per job; exec->c_mode, c_fixed, reflect, train, train_until_wpp and
    max_train_records apply to every job.  Pointers of the jobs are kept by
-   the plan and must stay valid until wost_batch_destroy. */
+   the plan and must stay valid until wost_batch_destroy.  The guided
+   autotuner also times 12 against 28 walker warps per CTA unless
+   exec->walker_warps fixes the count. */
 wost_status wost_batch_create(int32_t njobs, const wost_job *jobs, int32_t guided, const wost_exec *exec,
                               wost_batch **out);
 /* Replays the plan on stream (cudaStream_t, NULL = default stream) and

@@ -47,7 +47,8 @@ class Exec(C.Structure):
                 ("max_train_records", C.c_int64), ("walk_begin", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("guided_kernel", C.c_int32), ("wavefront_slots", C.c_int32),
                 ("train_samples", C.c_int64), ("rr_depth", C.c_int32), ("rr_survival", C.c_float),
-                ("wait_ns", C.c_int64), ("batch_wpp", C.c_int32)]
+                ("wait_ns", C.c_int64), ("batch_wpp", C.c_int32),
+                ("walker_warps", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -71,7 +72,8 @@ class Job(C.Structure):
 class BatchInfo(C.Structure):
     _fields_ = [("ctas_per_sm", C.c_int32), ("flush_polls", C.c_int32), ("candidates", C.c_int32),
                 ("best_ms", C.c_double), ("worst_ms", C.c_double), ("walk_launches", C.c_int32),
-                ("train_steps", C.c_int32), ("graph_nodes", C.c_int64)]
+                ("train_steps", C.c_int32), ("graph_nodes", C.c_int64),
+                ("walker_warps", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -14,8 +14,9 @@
 // classification, walk launches, training steps, per-point finalisation)
 // and replayed by wost_batch_run.  Before capture, an autotuner times the
 // candidate launch shapes on one calibration walk per point of every job:
-// resident CTAs per SM for the plain walk, and the decode-tile flush
-// threshold for the guided walk.
+// resident CTAs per SM for the plain walk; for the guided walk the walker
+// warps per CTA (12 or 28 beside the 4 decode servers: the queue of rows
+// that feeds a decode tile) and the decode-tile flush threshold.
 #include <algorithm>
 #include <cstring>
 #include <unordered_set>
@@ -51,10 +52,10 @@ __global__ void __launch_bounds__(kBatchPlainBlock) batch_plain_kernel(const __g
     plain_loop<D>(BatchSrc<D>{b}, b.stat);
 }
 
-template <int D>
-__global__ void __launch_bounds__(kWsThreads, 1) batch_guided_kernel(const __grid_constant__ BatchGuidedArgs g) {
+template <int D, int W>
+__global__ void __launch_bounds__(ws_threads(W), 1) batch_guided_kernel(const __grid_constant__ BatchGuidedArgs g) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    guided_ws_body<D, true>(BatchSrc<D>{g.b}, g.o, sm);
+    guided_ws_body<D, true, W>(BatchSrc<D>{g.b}, g.o, sm);
 }
 
 // job owning batch point i: the last job whose point_off <= i
@@ -129,6 +130,7 @@ struct wost_batch {
     wost_batch_info info{};
     int cps = 1;
     uint32_t polls = kFlushPolls;
+    int walkers = kWsWalkerWarps;
     int scratch_steps = 1;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -154,7 +156,8 @@ struct wost_batch {
         return b;
     }
 
-    wost_status launch_walk(const Launch &L, unsigned long long *work, cudaStream_t st, int cps_, uint32_t polls_) {
+    wost_status launch_walk(const Launch &L, unsigned long long *work, cudaStream_t st, int cps_, uint32_t polls_,
+                            int walkers_) {
         const BatchArgs b = args(L, work);
         if (!guided) {
             const int grid = num_sms() * cps_;
@@ -173,8 +176,12 @@ struct wost_batch {
             g.o.wait_ns = ex.wait_ns > 0 ? (unsigned long long)ex.wait_ns : kWaitNs;
             g.o.err = b.err;
             g.o.stat = b.stat;
-            if (dim == 2) batch_guided_kernel<2><<<num_sms(), kWsThreads, kBatchGuidedSmem, st>>>(g);
-            else batch_guided_kernel<3><<<num_sms(), kWsThreads, kBatchGuidedSmem, st>>>(g);
+            constexpr int tn = ws_threads(kWsWalkerWarps), tw = ws_threads(kWsWalkersWide);
+            const bool wide = walkers_ == kWsWalkersWide;
+            if (dim == 2 && wide) batch_guided_kernel<2, kWsWalkersWide><<<num_sms(), tw, kBatchGuidedSmem, st>>>(g);
+            else if (dim == 2) batch_guided_kernel<2, kWsWalkerWarps><<<num_sms(), tn, kBatchGuidedSmem, st>>>(g);
+            else if (wide) batch_guided_kernel<3, kWsWalkersWide><<<num_sms(), tw, kBatchGuidedSmem, st>>>(g);
+            else batch_guided_kernel<3, kWsWalkerWarps><<<num_sms(), tn, kBatchGuidedSmem, st>>>(g);
         }
         WOST_CUDA(cudaGetLastError());
         return WOST_OK;
@@ -196,7 +203,7 @@ struct wost_batch {
                 batch_rec_roll_kernel<<<blocks_of(nj, 64), 64, 0, st>>>(dj, nj, ctr_at(kCtrRec), rolled ? 1 : 0);
                 rolled = true;
             }
-            wost_status rc = launch_walk(L, ctr_at(kCtrWork + (int)l), st, cps, polls);
+            wost_status rc = launch_walk(L, ctr_at(kCtrWork + (int)l), st, cps, polls, walkers);
             if (rc != WOST_OK) return rc;
             for (int j : L.train_jobs) {
                 rc = train_launch(jobs[j].field, dim, st, true, nullptr);
@@ -212,19 +219,25 @@ struct wost_batch {
 
     // times the calibration launch under the candidate shapes; keeps the fastest
     wost_status autotune() {
-        std::vector<std::pair<int, uint32_t>> cand;
+        struct Cand { int cps; uint32_t polls; int walkers; };
+        std::vector<Cand> cand;
+        const int fixed_w = ex.walker_warps > 0 ? ex.walker_warps : kWsWalkerWarps;
         if (!guided) {
             int occ = 1;
             if (dim == 2) WOST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_plain_kernel<2>, kBatchPlainBlock, 0));
             else WOST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_plain_kernel<3>, kBatchPlainBlock, 0));
             occ = std::max(1, occ);
-            for (int c = 1; c <= occ; ++c) cand.push_back({c, kFlushPolls});
+            for (int c = 1; c <= occ; ++c) cand.push_back({c, kFlushPolls, kWsWalkerWarps});
         } else {
-            for (uint32_t p : {64u, 256u, 1024u}) cand.push_back({1, p});
+            for (int w : {kWsWalkerWarps, kWsWalkersWide}) {
+                if (ex.walker_warps > 0 && w != ex.walker_warps) continue;
+                for (uint32_t p : {64u, 256u, 1024u}) cand.push_back({1, p, w});
+            }
         }
         if (ex.ctas_per_sm > 0 || calib.total == 0) {
-            cps = ex.ctas_per_sm > 0 ? (guided ? 1 : std::min(ex.ctas_per_sm, cand.back().first)) : cand.back().first;
+            cps = ex.ctas_per_sm > 0 ? (guided ? 1 : std::min(ex.ctas_per_sm, cand.back().cps)) : cand.back().cps;
             polls = kFlushPolls;
+            walkers = fixed_w;
             info.candidates = 0;
             return WOST_OK;
         }
@@ -239,13 +252,13 @@ struct wost_batch {
             for (int rep = 0; rep < 2; ++rep) {   // first run warms the caches
                 WOST_CUDA(cudaMemsetAsync(ctr_at(kCtrCalib), 0, sizeof(unsigned long long), cap));
                 WOST_CUDA(cudaEventRecord(ev0, cap));
-                wost_status rc = launch_walk(calib, ctr_at(kCtrCalib), cap, c.first, c.second);
+                wost_status rc = launch_walk(calib, ctr_at(kCtrCalib), cap, c.cps, c.polls, c.walkers);
                 if (rc != WOST_OK) return rc;
                 WOST_CUDA(cudaEventRecord(ev1, cap));
             }
             WOST_CUDA(cudaEventSynchronize(ev1));
             WOST_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
-            if (ms < best) { best = ms; cps = c.first; polls = c.second; }
+            if (ms < best) { best = ms; cps = c.cps; polls = c.polls; walkers = c.walkers; }
             worst = std::max(worst, (double)ms);
         }
         wost_status rc = device_check(cap);
@@ -273,6 +286,10 @@ wost_status validate(int32_t njobs, const wost_job *jobs, int32_t guided, const 
     if (njobs <= 0 || !jobs) { set_error("wost_batch_create: no jobs"); return WOST_ERR_INVALID_ARG; }
     if (ex.rr_depth < 0 || (ex.rr_depth > 0 && !(ex.rr_survival > 0.f && ex.rr_survival <= 1.f))) {
         set_error("wost_batch_create: rr_depth must be >= 0 and rr_survival in (0, 1]");
+        return WOST_ERR_INVALID_ARG;
+    }
+    if (!ws_walker_warps_valid(ex.walker_warps)) {
+        set_error("wost_batch_create: walker_warps must be 0, 12 or 28");
         return WOST_ERR_INVALID_ARG;
     }
     const int dim = jobs[0].scene ? jobs[0].scene->dim : 0;
@@ -387,7 +404,9 @@ wost_status build_plan(wost_batch *p) {
     if ((rc = p->ctr.ensure((kCtrWork + p->launches.size() + 1) * sizeof(unsigned long long))) != WOST_OK) return rc;
     if (p->record) {
         p->scratch_steps = max_steps;
-        size_t sb = (size_t)num_sms() * kWsWalkerWarps * 32 * (size_t)max_steps * kRecFloats * sizeof(float);
+        // walker lanes of the widest launch a plan may choose
+        const int wmax = ex.walker_warps > 0 ? ex.walker_warps : kWsWalkersWide;
+        size_t sb = (size_t)num_sms() * wmax * 32 * (size_t)max_steps * kRecFloats * sizeof(float);
         if ((rc = p->scratch.ensure(sb)) != WOST_OK) return rc;
         for (int j = 0; j < nj; ++j) {
             wost_field *f = p->jobs[j].field;
@@ -406,8 +425,14 @@ wost_status build_plan(wost_batch *p) {
     for (auto &L : p->launches) p->info.train_steps += (int)L.train_jobs.size();
     p->info.walk_launches = (int)p->launches.size();
     if (p->guided) {
-        if (D == 2) WOST_CUDA(cudaFuncSetAttribute(batch_guided_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchGuidedSmem));
-        else WOST_CUDA(cudaFuncSetAttribute(batch_guided_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchGuidedSmem));
+        const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if (D == 2) {
+            WOST_CUDA(cudaFuncSetAttribute(batch_guided_kernel<2, kWsWalkerWarps>, at, kBatchGuidedSmem));
+            WOST_CUDA(cudaFuncSetAttribute(batch_guided_kernel<2, kWsWalkersWide>, at, kBatchGuidedSmem));
+        } else {
+            WOST_CUDA(cudaFuncSetAttribute(batch_guided_kernel<3, kWsWalkerWarps>, at, kBatchGuidedSmem));
+            WOST_CUDA(cudaFuncSetAttribute(batch_guided_kernel<3, kWsWalkersWide>, at, kBatchGuidedSmem));
+        }
     }
     device_err_flag();   // created outside the capture
     WOST_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
@@ -416,6 +441,7 @@ wost_status build_plan(wost_batch *p) {
     if ((rc = p->autotune()) != WOST_OK) return rc;
     p->info.ctas_per_sm = p->guided ? 1 : p->cps;
     p->info.flush_polls = (int)p->polls;
+    p->info.walker_warps = p->guided ? p->walkers : 0;
     if (p->total_points == 0) return WOST_OK;
     // capture
     WOST_CUDA(cudaStreamSynchronize(p->cap));

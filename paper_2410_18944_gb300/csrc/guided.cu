@@ -21,9 +21,10 @@ struct GuidedArgs {
     int stage_mask;    // scene regions staged in shared memory (stage_plan)
 };
 
-// Walker warps of the single-scene kernel: kWsWalkerWarps (12) when the
-// scene's traversal data (BVH nodes, cones, primitives) fits comfortably in
-// L2 or shared memory, kWsWalkersWide beside the 4 servers when it does not.
+// Walker warps of the single-scene kernel (exec walker_warps 0): kWsWalkerWarps
+// (12) when the scene's traversal data (BVH nodes, cones, primitives) fits
+// comfortably in L2 or shared memory, kWsWalkersWide beside the 4 servers
+// when it does not.
 // Measured on one GB300, one recording round: genus-3 solid (about 300 MB of
 // traversal data) 1057 ms with 12 walker warps, 964 with 14, 798 with 20,
 // 729 with 24, 695 with 28 (32 warps, the 1024-thread limit); icosphere of
@@ -31,10 +32,6 @@ struct GuidedArgs {
 // walkers hide the latency of BVH loads that miss L2; with the scene in L2
 // the register cap they impose (64 per thread at 1024 threads, with spills)
 // costs more than it hides.
-#ifndef WOST_WS_WALKERS_WIDE
-#define WOST_WS_WALKERS_WIDE 28
-#endif
-constexpr int kWsWalkersWide = WOST_WS_WALKERS_WIDE;
 #ifndef WOST_WS_WIDE_MB
 #define WOST_WS_WIDE_MB 64
 #endif
@@ -60,10 +57,14 @@ static size_t traversal_bytes(const DevScene &s) {
            ps * (size_t)s.sil.nprims + 16 * (size_t)bvh_width(s.dim) * s.sil.nnodes;
 }
 
-// the walker-warp count of a scene's guided launches
-static int ws_walkers_for(const DevScene &s) {
+// the walker-warp count of a scene's guided launches (`req`: the caller's
+// choice, 0 = by the size of the scene's traversal data)
+static int ws_walkers_for(const DevScene &s, int req) {
+    if (req > 0) return req;
     return traversal_bytes(s) > ((size_t)WOST_WS_WIDE_MB << 20) ? kWsWalkersWide : kWsWalkerWarps;
 }
+
+bool ws_walker_warps_valid(int w) { return w == 0 || w == kWsWalkerWarps || w == kWsWalkersWide; }
 
 // decode of arbitrary points: the same tile forward as inside the walk
 template <int D>
@@ -187,11 +188,11 @@ static int stage_mask_for(const DevScene &sc, int *f4) {
     return stage_plan(sc, stage_budget_bytes() / 16, f4);
 }
 
-wost_status launch_guided(int dim, const GuidedArgs &g, int grid, cudaStream_t st) {
+wost_status launch_guided(int dim, const GuidedArgs &g, int grid, cudaStream_t st, int walkers) {
     int f4 = 0;
     stage_mask_for(g.w.sc, &f4);
     const int smem = kWsSmem + f4 * 16;
-    const bool wide = ws_walkers_for(g.w.sc) == kWsWalkersWide;
+    const bool wide = walkers == kWsWalkersWide;
     constexpr int tn = ws_threads(kWsWalkerWarps), tw = ws_threads(kWsWalkersWide);
     if (dim == 2 && wide) guided_walk_kernel<2, kWsWalkersWide><<<grid, tw, smem, st>>>(g);
     else if (dim == 2) guided_walk_kernel<2, kWsWalkerWarps><<<grid, tn, smem, st>>>(g);
@@ -263,7 +264,7 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
         int k = 0;
         wost_status rc = train_after_batch(f, s->dim, st, &k);
         tm.mark(tm.train, st);
-        tm.launches += 5 * k;   // per step: gradient, Adam step count, Adam, FP16 grid copy, BF16 weight image
+        tm.launches += 4 * k;   // per step: gradient, Adam step count, Adam (and the FP16 grid copy), BF16 weight image
         ntrain += k;
         return rc;
     };
@@ -303,9 +304,10 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
         if (orc != WOST_OK) return orc;
         int cps = ex.ctas_per_sm > 0 ? std::min(ex.ctas_per_sm, occ) : occ;
         int grid = num_sms() * cps;
+        const int walkers = ws_walkers_for(s->dev, ex.walker_warps);
         if (rounds > 0) {
-            size_t scratch = (size_t)grid * (ws_walkers_for(s->dev) * 32) * (size_t)std::max(a.maxsteps, 1) *
-                             kRecFloats * sizeof(float);
+            size_t scratch = (size_t)grid * (walkers * 32) * (size_t)std::max(a.maxsteps, 1) * kRecFloats *
+                             sizeof(float);
             wost_status rc = ensure_records(f, rec_cap, scratch);
             if (rc != WOST_OK) return rc;
             g.rd = RecDest{f->rec, f->rec_ctr, f->rec_cap};
@@ -324,7 +326,7 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
             WOST_CUDA(cudaMemsetAsync(a.work_ctr, 0, sizeof(unsigned long long), st));
             if (g.o.record) WOST_CUDA(cudaMemsetAsync(f->rec_ctr, 0, 2 * sizeof(unsigned long long), st));
             tm.mark(tm.walk, st);
-            wost_status rc = launch_guided(s->dim, g, grid, st);
+            wost_status rc = launch_guided(s->dim, g, grid, st, walkers);
             tm.mark(tm.walk, st);
             tm.launches++;
             tm.walk_launches++;

@@ -56,6 +56,14 @@ constexpr int kWsServerWarps = 4;
 #define WOST_WS_TILES 1
 #endif
 constexpr int kWsWalkerWarps = WOST_WS_WALKERS;
+// Walker warps of the wide variant, for scenes whose traversal data misses
+// L2: more walkers hide the latency of BVH loads from HBM (32 warps at 28,
+// the 1024-thread limit; 64 registers per thread).
+#ifndef WOST_WS_WALKERS_WIDE
+#define WOST_WS_WALKERS_WIDE 28
+#endif
+constexpr int kWsWalkersWide = WOST_WS_WALKERS_WIDE;
+static_assert(kWsServerWarps + kWsWalkersWide <= 32, "a CTA holds at most 32 warps");
 // threads of a CTA with W walker warps beside the decode servers
 __host__ __device__ constexpr int ws_threads(int W) { return 32 * (kWsServerWarps + W); }
 constexpr int kWsThreads = ws_threads(kWsWalkerWarps);

@@ -87,4 +87,6 @@ wost_status device_check(cudaStream_t st);
 // `who`.  Called before any launch: a kernel on the wrong device would read
 // another GPU's pointers.
 wost_status check_device(int device, const char *who);
+// walker warps a guided launch may take (exec walker_warps: 0 = automatic)
+bool ws_walker_warps_valid(int w);
 }

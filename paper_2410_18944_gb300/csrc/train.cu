@@ -361,20 +361,57 @@ struct AdamGroup {
 
 __global__ void adam_tick_kernel(unsigned long long *t) { *t += 1; }
 
-__global__ void adam_kernel(AdamGroup ga, AdamGroup gb, int nb_a, float b1, float b2, float eps,
-                            const unsigned long long *t_dev) {
+// Four elements per thread (16-byte accesses; the arrays are separate
+// allocations, so 16-byte aligned); the grid group also writes the FP16
+// inference copy of the entries it updated (grid16[e] = features 2e, 2e + 1).
+constexpr int kAdamBlock = 256;
+constexpr int kAdamPer = 4;
+
+__device__ __forceinline__ float adam_one(float &p, float g, float &m, float &v, float b1, float b2, float c1,
+                                          float c2, float lr, float eps) {
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    p -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+    return p;
+}
+
+__global__ void __launch_bounds__(kAdamBlock) adam_kernel(AdamGroup ga, AdamGroup gb, int nb_a, float b1, float b2,
+                                                          float eps, const unsigned long long *t_dev,
+                                                          __half2 *grid16) {
+    __shared__ float corr[2];
+    if (threadIdx.x == 0) {
+        const float t = (float)*t_dev;
+        corr[0] = 1.f - powf(b1, t);
+        corr[1] = 1.f - powf(b2, t);
+    }
+    __syncthreads();
+    const float c1 = corr[0], c2 = corr[1];
     const bool first = (int)blockIdx.x < nb_a;
     const AdamGroup &G = first ? ga : gb;
-    int64_t i = (int64_t)(first ? blockIdx.x : blockIdx.x - nb_a) * blockDim.x + threadIdx.x;
+    const int64_t i = ((int64_t)(first ? blockIdx.x : blockIdx.x - nb_a) * blockDim.x + threadIdx.x) * kAdamPer;
     if (i >= G.n) return;
-    const float t = (float)*t_dev;
-    const float c1 = 1.f - powf(b1, t), c2 = 1.f - powf(b2, t);
-    float gi = G.g[i];
-    float mi = b1 * G.m[i] + (1.f - b1) * gi;
-    float vi = b2 * G.v[i] + (1.f - b2) * gi * gi;
-    G.m[i] = mi;
-    G.v[i] = vi;
-    G.p[i] -= G.lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    if (i + kAdamPer <= G.n) {
+        float4 p = *reinterpret_cast<const float4 *>(G.p + i), g = *reinterpret_cast<const float4 *>(G.g + i);
+        float4 m = *reinterpret_cast<const float4 *>(G.m + i), v = *reinterpret_cast<const float4 *>(G.v + i);
+        adam_one(p.x, g.x, m.x, v.x, b1, b2, c1, c2, G.lr, eps);
+        adam_one(p.y, g.y, m.y, v.y, b1, b2, c1, c2, G.lr, eps);
+        adam_one(p.z, g.z, m.z, v.z, b1, b2, c1, c2, G.lr, eps);
+        adam_one(p.w, g.w, m.w, v.w, b1, b2, c1, c2, G.lr, eps);
+        *reinterpret_cast<float4 *>(G.p + i) = p;
+        *reinterpret_cast<float4 *>(G.m + i) = m;
+        *reinterpret_cast<float4 *>(G.v + i) = v;
+        if (first) {
+            grid16[i / 2] = __floats2half2_rn(p.x, p.y);
+            grid16[i / 2 + 1] = __floats2half2_rn(p.z, p.w);
+        }
+        return;
+    }
+    // the ragged end (the grid holds an even number of floats)
+    float q[kAdamPer];
+    const int r = (int)(G.n - i);
+    for (int j = 0; j < r; ++j) q[j] = adam_one(G.p[i + j], G.g[i + j], G.m[i + j], G.v[i + j], b1, b2, c1, c2, G.lr, eps);
+    if (first)
+        for (int j = 0; j + 1 < r; j += 2) grid16[(i + j) / 2] = __floats2half2_rn(q[j], q[j + 1]);
 }
 
 __global__ void grid_to_half_kernel(const float *g32, __half2 *g16, int64_t n) {
@@ -407,13 +444,19 @@ __global__ void weight_image_kernel(const float *mlp, int nout, int dim, int K, 
     }
 }
 
-wost_status refresh_inference_copy(wost_field *f, cudaStream_t st) {
-    const int64_t ne = f->level_off[f->desc.levels];   // lattice entries of all levels (either encoding)
-    grid_to_half_kernel<<<(int)((ne + 255) / 256), 256, 0, st>>>(f->grid32, f->grid16, ne);
+// BF16 weight image and padded bias from the FP32 MLP masters
+static wost_status refresh_weight_image(wost_field *f, cudaStream_t st) {
     weight_image_kernel<<<(kHid * kHid + 255) / 256, 256, 0, st>>>(f->mlp32, f->nout, f->desc.dim, f->desc.K,
                                                                     f->wimg, f->b3pad);
     WOST_CUDA(cudaGetLastError());
     return WOST_OK;
+}
+
+wost_status refresh_inference_copy(wost_field *f, cudaStream_t st) {
+    const int64_t ne = f->level_off[f->desc.levels];   // lattice entries of all levels (either encoding)
+    grid_to_half_kernel<<<(int)((ne + 255) / 256), 256, 0, st>>>(f->grid32, f->grid16, ne);
+    WOST_CUDA(cudaGetLastError());
+    return refresh_weight_image(f, st);
 }
 
 // one-time kernel attributes (also called before a stream capture, where
@@ -488,11 +531,13 @@ wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_ada
     int64_t ng = f->n_grid(), nm = f->n_mlp();
     AdamGroup ga{f->grid32, f->grid_g, f->grid_m, f->grid_v, ng, d.lr_grid};
     AdamGroup gb{f->mlp32, f->mlp_g, f->mlp_m, f->mlp_v, nm, d.lr_mlp};
-    const int nba = (int)((ng + 255) / 256), nbb = (int)((nm + 255) / 256);
+    constexpr int per_block = kAdamBlock * kAdamPer;
+    const int nba = (int)((ng + per_block - 1) / per_block), nbb = (int)((nm + per_block - 1) / per_block);
     adam_tick_kernel<<<1, 1, 0, st>>>(f->adam_step());
-    adam_kernel<<<nba + nbb, 256, 0, st>>>(ga, gb, nba, d.beta1, d.beta2, d.adam_eps, f->adam_step());
+    adam_kernel<<<nba + nbb, kAdamBlock, 0, st>>>(ga, gb, nba, d.beta1, d.beta2, d.adam_eps, f->adam_step(),
+                                                  f->grid16);
     WOST_CUDA(cudaGetLastError());
-    return refresh_inference_copy(f, st);
+    return refresh_weight_image(f, st);   // the FP16 grid copy came with the update
 }
 
 // Training after a batch of wost_solve (Sec. 5.2): one Adam step on every

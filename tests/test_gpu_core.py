@@ -470,6 +470,8 @@ def test_training_batches_of_several_walks_per_point(api):
     assert np.all(np.isfinite(m)) and np.mean(np.abs(z) < 4.0) > 0.98
     with pytest.raises(Exception):
         api.solve(S, pts, 2, field=F, train=1, batch_wpp=-1, **common)
+    with pytest.raises(Exception):
+        api.solve(S, pts, 2, field=F, walker_warps=20, **common)
 
 
 def test_guided_walks_stay_inside_star(api):
@@ -520,16 +522,17 @@ def test_wavefront_equals_warp_specialised(api, dim):
     # the two guided kernels draw the same random numbers and decode the same
     # FP16 rows, so with a frozen field their estimates agree up to the order
     # of the FP64 atomic sums; more walks than slots exercises slot refill,
-    # and the automatic choice runs a frozen solve on the wavefront
+    # the warp-specialised kernel runs with 12 and 28 walker warps, and the
+    # automatic choice runs a frozen solve on the wavefront
     sc = wi.star_polyline(512, seed=3) if dim == 2 else wi.displaced_icosphere(subdiv=3, seed=4)
     S = api.Scene(sc)
     F, _, _ = _field_pair(api, dim, 21, sc, w_scale=1.2)
     pts = _interior(sc, 300, 13, margin=0.02)
     pd = torch.tensor(pts, dtype=torch.float64, device="cuda")
     out = []
-    for kern, slots in ((1, 0), (2, 0), (2, 1000), (0, 0)):
+    for kern, slots, ww in ((1, 0, 0), (1, 0, 28), (2, 0, 0), (2, 1000, 0), (0, 0, 0)):
         m, v, st = api.solve(S, pd, 24, eps=1e-3, maxsteps=256, guided=True, field=F, seed=31, guided_kernel=kern,
-                             wavefront_slots=slots)
+                             wavefront_slots=slots, walker_warps=ww)
         out.append((m.cpu().numpy(), v.cpu().numpy(), st))
     m1, v1, s1 = out[0]
     for m0, v0, s0 in out[1:]:
