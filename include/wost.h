@@ -169,8 +169,10 @@ typedef struct {
                                   per CTA beside its 4 decode-server warps, 0 (automatic), 12 or
                                   28 (WOST_ERR_INVALID_ARG otherwise).  Automatic: wost_solve takes
                                   28 when the scene's traversal data (BVH nodes, cones,
-                                  primitives) exceeds 64 MB, else 12; wost_batch_create lets its
-                                  autotuner choose.  Results do not depend on it */
+                                  primitives) exceeds 64 MB or, in 3D, when a launch holds at
+                                  least two walks per lane of the 28-warp kernel, else 12;
+                                  wost_batch_create lets its autotuner choose.  Results do not
+                                  depend on it */
 } wost_exec;
 
 typedef struct {

@@ -57,11 +57,20 @@ static size_t traversal_bytes(const DevScene &s) {
            ps * (size_t)s.sil.nprims + 16 * (size_t)bvh_width(s.dim) * s.sil.nnodes;
 }
 
-// the walker-warp count of a scene's guided launches (`req`: the caller's
-// choice, 0 = by the size of the scene's traversal data)
-static int ws_walkers_for(const DevScene &s, int req) {
+// the walker-warp count of a scene's guided launches of `walks` walks
+// (`req`: the caller's choice, 0 = automatic): the wide kernel where the
+// scene's traversal data misses L2, or, in 3D, where a launch gives each of
+// its lanes about two walks or more (3D steps are long chains of dependent
+// loads that more warps hide; a launch with fewer walks leaves the wide
+// kernel's lanes idle and its register cap costs more).  Measured on one
+// GB300: icosphere of 82k triangles, batches of 8 walks per point (376k
+// walks) 400 ms with 12 walker warps, 357 with 28; one walk per point
+// (47k walks) 168 / 174 ms with 12 / 20; the 2D star equal (58 / 59 ms).
+static int ws_walkers_for(const DevScene &s, int req, unsigned long long walks) {
     if (req > 0) return req;
-    return traversal_bytes(s) > ((size_t)WOST_WS_WIDE_MB << 20) ? kWsWalkersWide : kWsWalkerWarps;
+    if (traversal_bytes(s) > ((size_t)WOST_WS_WIDE_MB << 20)) return kWsWalkersWide;
+    const unsigned long long wide_lanes = (unsigned long long)num_sms() * kWsWalkersWide * 32;
+    return s.dim == 3 && walks >= 2 * wide_lanes ? kWsWalkersWide : kWsWalkerWarps;
 }
 
 bool ws_walker_warps_valid(int w) { return w == 0 || w == kWsWalkerWarps || w == kWsWalkersWide; }
@@ -134,6 +143,7 @@ __global__ void mixture_sample_kernel(int K, const float *mu, const float *kap, 
 wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *loss_out_dev,
                          long long off = -1);
 wost_status train_after_batch(wost_field *f, int dim, cudaStream_t st, int *steps);
+int train_step_launches(const wost_field *f);
 
 int guided_ctas_per_sm() { return 1; }
 
@@ -264,7 +274,7 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
         int k = 0;
         wost_status rc = train_after_batch(f, s->dim, st, &k);
         tm.mark(tm.train, st);
-        tm.launches += 4 * k;   // per step: gradient, Adam step count, Adam (and the FP16 grid copy), BF16 weight image
+        tm.launches += train_step_launches(f) * k;
         ntrain += k;
         return rc;
     };
@@ -304,7 +314,9 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
         if (orc != WOST_OK) return orc;
         int cps = ex.ctas_per_sm > 0 ? std::min(ex.ctas_per_sm, occ) : occ;
         int grid = num_sms() * cps;
-        const int walkers = ws_walkers_for(s->dev, ex.walker_warps);
+        // the largest launch of the solve: a training batch, or one walk per point
+        const int walkers = ws_walkers_for(s->dev, ex.walker_warps,
+                                           (unsigned long long)a.npoints * (unsigned long long)(rounds > 0 ? bwpp : 1));
         if (rounds > 0) {
             size_t scratch = (size_t)grid * (walkers * 32) * (size_t)std::max(a.maxsteps, 1) * kRecFloats *
                              sizeof(float);

@@ -168,7 +168,8 @@ __device__ __forceinline__ bool named_or(int id, int count, bool pred) {
 }
 
 // 8 consecutive bf16 of one row into a core-matrix tile (16-byte store)
-__device__ __forceinline__ void st_row8_bf16(uint8_t *tile, int r, int c8, int C, const float *v) {
+// 8 floats as BF16 (round to nearest even), in order
+__device__ __forceinline__ uint4 pack8_bf16(const float *v) {
     __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
     __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
     uint4 u;
@@ -176,7 +177,11 @@ __device__ __forceinline__ void st_row8_bf16(uint8_t *tile, int r, int c8, int C
     u.y = *reinterpret_cast<uint32_t *>(&p1);
     u.z = *reinterpret_cast<uint32_t *>(&p2);
     u.w = *reinterpret_cast<uint32_t *>(&p3);
-    *reinterpret_cast<uint4 *>(tile + cm_offset(r, c8, C)) = u;
+    return u;
+}
+
+__device__ __forceinline__ void st_row8_bf16(uint8_t *tile, int r, int c8, int C, const float *v) {
+    *reinterpret_cast<uint4 *>(tile + cm_offset(r, c8, C)) = pack8_bf16(v);
 }
 
 __device__ __forceinline__ void ld_row8_bf16(const uint8_t *tile, int r, int c8, int C, float *v) {
