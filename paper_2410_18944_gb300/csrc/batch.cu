@@ -231,7 +231,7 @@ struct wost_batch {
         } else {
             for (int w : {kWsWalkerWarps, kWsWalkersWide}) {
                 if (ex.walker_warps > 0 && w != ex.walker_warps) continue;
-                for (uint32_t p : {64u, 256u, 1024u}) cand.push_back({1, p, w});
+                for (uint32_t p : {256u, 1024u, 4096u}) cand.push_back({1, p, w});
             }
         }
         if (ex.ctas_per_sm > 0 || calib.total == 0) {

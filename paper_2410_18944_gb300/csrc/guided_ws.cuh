@@ -94,10 +94,14 @@ constexpr int ws_smem_bytes(bool multi) {
     return kWImgBytes * ws_weight_slots(multi) + kNT * kBufBytes + kWsCtrlBytes +
            (multi ? kNT * (128 * 4 + kYBytes) : 0);
 }
+// Server polls before closing a partial tile.  Fuller tiles measured faster
+// (one GB300, training batches: icosphere 374 / 364 / 354 / 339-347 / 335 ms
+// with 1 / 32 / 256 / 1024 / 4096 polls, genus-3 708 / 703 / 696 / 688-691 /
+// 697, the 2D star 58 ms from 256 polls on and 65-67 below).
 #ifndef WOST_FLUSH_POLLS
-#define WOST_FLUSH_POLLS 256
+#define WOST_FLUSH_POLLS 1024
 #endif
-constexpr uint32_t kFlushPolls = WOST_FLUSH_POLLS;   // server polls before closing a partial tile
+constexpr uint32_t kFlushPolls = WOST_FLUSH_POLLS;
 // optional bound in time on the wait for a partial tile (0: polls only)
 #ifndef WOST_FLUSH_NS
 #define WOST_FLUSH_NS 0
