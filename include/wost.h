@@ -166,11 +166,11 @@ typedef struct {
                                   records; the walks past train_until_wpp are not batched.  The
                                   random numbers of a walk do not depend on the grouping */
     int32_t walker_warps;      /* guided launches of the warp-specialised kernel: walker warps
-                                  per CTA beside its 4 decode-server warps, 0 (automatic), 12 or
+                                  per CTA beside its 4 decode-server warps, 0 (automatic), 16 or
                                   28 (WOST_ERR_INVALID_ARG otherwise).  Automatic: wost_solve takes
                                   28 when the scene's traversal data (BVH nodes, cones,
                                   primitives) exceeds 64 MB or, in 3D, when a launch holds at
-                                  least two walks per lane of the 28-warp kernel, else 12;
+                                  least two walks per lane of the 28-warp kernel, else 16;
                                   wost_batch_create lets its autotuner choose.  Results do not
                                   depend on it */
 } wost_exec;
@@ -365,7 +365,7 @@ typedef struct {
    per job; exec->c_mode, c_fixed, reflect, train, train_until_wpp and
    max_train_records apply to every job.  Pointers of the jobs are kept by
    the plan and must stay valid until wost_batch_destroy.  The guided
-   autotuner also times 12 against 28 walker warps per CTA unless
+   autotuner also times 16 against 28 walker warps per CTA unless
    exec->walker_warps fixes the count. */
 wost_status wost_batch_create(int32_t njobs, const wost_job *jobs, int32_t guided, const wost_exec *exec,
                               wost_batch **out);

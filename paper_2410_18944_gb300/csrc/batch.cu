@@ -15,7 +15,7 @@
 // and replayed by wost_batch_run.  Before capture, an autotuner times the
 // candidate launch shapes on one calibration walk per point of every job:
 // resident CTAs per SM for the plain walk; for the guided walk the walker
-// warps per CTA (12 or 28 beside the 4 decode servers: the queue of rows
+// warps per CTA (16 or 28 beside the 4 decode servers: the queue of rows
 // that feeds a decode tile) and the decode-tile flush threshold.
 #include <algorithm>
 #include <cstring>
@@ -289,7 +289,7 @@ wost_status validate(int32_t njobs, const wost_job *jobs, int32_t guided, const 
         return WOST_ERR_INVALID_ARG;
     }
     if (!ws_walker_warps_valid(ex.walker_warps)) {
-        set_error("wost_batch_create: walker_warps must be 0, 12 or 28");
+        set_error("wost_batch_create: walker_warps must be 0, 16 or 28");
         return WOST_ERR_INVALID_ARG;
     }
     const int dim = jobs[0].scene ? jobs[0].scene->dim : 0;

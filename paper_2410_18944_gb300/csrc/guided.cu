@@ -22,7 +22,7 @@ struct GuidedArgs {
 };
 
 // Walker warps of the single-scene kernel (exec walker_warps 0): kWsWalkerWarps
-// (12) when the scene's traversal data (BVH nodes, cones, primitives) fits
+// (16) when the scene's traversal data (BVH nodes, cones, primitives) fits
 // comfortably in L2 or shared memory, kWsWalkersWide beside the 4 servers
 // when it does not.
 // Measured on one GB300, one recording round: genus-3 solid (about 300 MB of
@@ -147,7 +147,7 @@ int train_step_launches(const wost_field *f);
 
 int guided_ctas_per_sm() { return 1; }
 
-// The warp-specialised walk kernel runs one CTA (512 threads) per SM; its
+// The warp-specialised walk kernel runs one CTA (640 or 1024 threads) per SM; its
 // dynamic shared memory holds the decode tiles and as much of the scene's
 // traversal data as fits (stage_plan), at most WOST_STAGE_MAX_KB.
 #ifndef WOST_STAGE_MAX_KB

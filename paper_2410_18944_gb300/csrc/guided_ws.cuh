@@ -49,8 +49,14 @@
 namespace wost {
 
 constexpr int kWsServerWarps = 4;
+// Walker warps of the standard variant (640 threads, 102 registers each).
+// Measured on one GB300, training batches of the bench: 2D star 58.1 /
+// 55.0 / 55.2 / 57.5 / 59.5 ms with 12 / 16 / 20 / 24 / 28 walker warps,
+// icosphere 403 / 340 / 335 / 341 / 334-357 ms (the latter run by the wide
+// variant); fewer warps hide less latency, more impose a register cap that
+// spills.
 #ifndef WOST_WS_WALKERS
-#define WOST_WS_WALKERS 12
+#define WOST_WS_WALKERS 16
 #endif
 #ifndef WOST_WS_TILES
 #define WOST_WS_TILES 1

@@ -226,7 +226,7 @@ extern "C" wost_status wost_solve(wost_scene *s, wost_field *field, const double
     }
     if (exec && exec->batch_wpp < 0) { set_error("wost_solve: batch_wpp must be >= 0"); return WOST_ERR_INVALID_ARG; }
     if (exec && !ws_walker_warps_valid(exec->walker_warps)) {
-        set_error("wost_solve: walker_warps must be 0, 12 or 28");
+        set_error("wost_solve: walker_warps must be 0, 16 or 28");
         return WOST_ERR_INVALID_ARG;
     }
     {

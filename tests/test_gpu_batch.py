@@ -125,7 +125,7 @@ def test_guided_frozen_batch_equals_separate_solves(api, dim):
 
 
 def test_guided_plan_tunes_the_walker_count(api):
-    # the autotuner times 12 and 28 walker warps (three flush thresholds
+    # the autotuner times 16 and 28 walker warps (three flush thresholds
     # each) unless exec fixes the count; either way the plan's results equal
     # those of the same plan at the other count
     jobs = _small_star_jobs(4, seed=53, pts=(40, 400), wpp=(2, 4))
@@ -133,11 +133,11 @@ def test_guided_plan_tunes_the_walker_count(api):
                   field=_field(api, 2, 500 + i, j.scene, w_scale=1.2)) for i, j in enumerate(jobs)]
     b = api.Batch(specs, guided=True, train=0)
     info = b.info()
-    assert info["candidates"] == 6 and info["walker_warps"] in (12, 28)
+    assert info["candidates"] == 6 and info["walker_warps"] in (16, 28)
     b.run()
     m_auto = [m.cpu().numpy().copy() for m in b.mean]
     b.close()
-    other = 40 - info["walker_warps"]
+    other = 16 + 28 - info["walker_warps"]
     b2 = api.Batch(specs, guided=True, train=0, walker_warps=other)
     info2 = b2.info()
     assert info2["candidates"] == 3 and info2["walker_warps"] == other
@@ -146,7 +146,7 @@ def test_guided_plan_tunes_the_walker_count(api):
         assert np.allclose(a, m.cpu().numpy(), rtol=1e-9, atol=1e-12)
     b2.close()
     with pytest.raises(Exception):
-        api.Batch(specs, guided=True, train=0, walker_warps=16)
+        api.Batch(specs, guided=True, train=0, walker_warps=20)
 
 
 def test_guided_training_batch_is_unbiased(api):

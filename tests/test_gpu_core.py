@@ -522,7 +522,7 @@ def test_wavefront_equals_warp_specialised(api, dim):
     # the two guided kernels draw the same random numbers and decode the same
     # FP16 rows, so with a frozen field their estimates agree up to the order
     # of the FP64 atomic sums; more walks than slots exercises slot refill,
-    # the warp-specialised kernel runs with 12 and 28 walker warps, and the
+    # the warp-specialised kernel runs with 16 and 28 walker warps, and the
     # automatic choice runs a frozen solve on the wavefront
     sc = wi.star_polyline(512, seed=3) if dim == 2 else wi.displaced_icosphere(subdiv=3, seed=4)
     S = api.Scene(sc)
