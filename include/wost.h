@@ -50,7 +50,7 @@ typedef enum {
     WOST_ERR_CUDA = 3,         /* CUDA runtime error (message has details) */
     WOST_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
     WOST_ERR_OOM = 5,          /* device allocation failed */
-    WOST_ERR_UNSUPPORTED = 6   /* valid but not supported by this build (e.g. a field shape) */
+    WOST_ERR_UNSUPPORTED = 6   /* valid but not supported by this library (e.g. a field shape) */
 } wost_status;
 
 /* Analytic data functions g (Dirichlet), f (source), h (Neumann flux).
@@ -93,7 +93,7 @@ typedef struct wost_field wost_field;
 /* Neural field of the guiding distribution (Sec. 5.2): L levels of a hash
    grid (2^log2_table entries x F features, FP32 master + FP16 copy), MLP
    (L F) -> H -> H -> (d + 2) K + 1 with ReLU, BF16 operands, FP32
-   accumulation.  Fixed in this build: F = 2, L * F = 32, H = 64; K = 1..8
+   accumulation.  Fixed in this library: F = 2, L * F = 32, H = 64; K = 1..8
    lobes (8 by default; the lobe-count ablation of Sec. 6.3 uses 4 and 8).
    Positions are mapped to [0,1]^d by the box [lo, hi]. */
 typedef struct {

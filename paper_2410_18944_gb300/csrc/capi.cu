@@ -172,7 +172,7 @@ extern "C" wost_status wost_create_field(const wost_field_desc *desc, wost_field
     *out = nullptr;
     const wost_field_desc &d = *desc;
     if ((d.dim != 2 && d.dim != 3) || d.K < 1 || d.K > kMaxK || d.levels != 16 || d.features != 2 || d.hidden != 64) {
-        set_error("wost_create_field: this build supports dim 2/3, K = 1..8, L = 16, F = 2, H = 64");
+        set_error("wost_create_field: this library supports dim 2/3, K = 1..8, L = 16, F = 2, H = 64");
         return WOST_ERR_UNSUPPORTED;
     }
     if (d.log2_table < 8 || d.log2_table > 24 || d.base_res < 2 || d.max_res < d.base_res ||
