@@ -240,7 +240,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
     const uint32_t tmem0 = ctl->tmem;
 
     Visits vis;
-    uint32_t nsteps = 0, ntrunc = 0, nwalks = 0;   // per thread: far below 2^32
+    unsigned long long nsteps = 0, ntrunc = 0, nwalks = 0;
 
     if (warp < kWsServerWarps) {
         // ------------------------------ server ------------------------------

@@ -351,6 +351,20 @@ def test_train_gradient_parity(api, dim, kind):
             assert cos > 0.99995 and rel < 1e-2, (name, cos, rel)
         else:
             assert cos > 0.998 and rel < 6e-2, (name, cos, rel)
+    # the training scatter of the coarse levels goes to several copies of
+    # their gradient inside the unused entries of the level's table and sums
+    # them back: those entries (past (N_l + 1)^d of a densely indexed level)
+    # must come out exactly zero, as in the oracle
+    d = F.desc
+    T = 1 << d.log2_table
+    g = gg["grid"].reshape(d.levels, T, d.features)
+    dense_levels = 0
+    for l, n in enumerate(wi.level_resolutions(d.levels, d.base_res, d.max_res)):
+        V = (n + 1) ** dim
+        if V <= T:
+            dense_levels += 1
+            assert not np.any(g[l, V:]), (l, V, np.count_nonzero(g[l, V:]))
+    assert dense_levels >= 4
 
 
 @pytest.mark.parametrize("dim", [2, 3])
