@@ -93,12 +93,18 @@ typedef struct wost_field wost_field;
 /* Neural field of the guiding distribution (Sec. 5.2): L levels of a hash
    grid (2^log2_table entries x F features, FP32 master + FP16 copy), MLP
    (L F) -> H -> H -> (d + 2) K + 1 with ReLU, BF16 operands, FP32
-   accumulation.  Fixed in this library: F = 2, L * F = 32, H = 64; K = 1..8
-   lobes (8 by default; the lobe-count ablation of Sec. 6.3 uses 4 and 8).
+   accumulation.  Fixed in this library: F = 2, L * F = 32, H = 64; K = 1..16
+   lobes (8 by default; the lobe-count ablation of Sec. 6.3 compares 4, 8
+   and 16).  Fields of 9..16 lobes are served by 16-lobe variants of the
+   kernels: their guided walks always run the warp-specialised kernel with
+   the standard walker count (exec guided_kernel 2 or a wide walker_warps
+   give WOST_ERR_UNSUPPORTED), their training step runs one 128-record tile
+   per SM instead of two, and many-scene batches reject them
+   (WOST_ERR_UNSUPPORTED).
    Positions are mapped to [0,1]^d by the box [lo, hi]. */
 typedef struct {
     int32_t dim;
-    int32_t K;                 /* lobes (1..8, default 8) */
+    int32_t K;                 /* lobes (1..16, default 8) */
     int32_t levels;            /* L (16) */
     int32_t log2_table;        /* log2 of entries per level */
     int32_t features;          /* F (2) */
@@ -305,8 +311,8 @@ wost_status wost_query_ray(wost_scene *scene, const double *org, const double *d
 wost_status wost_query_ray_exit(wost_scene *scene, const double *org, const double *dir,
                                 const double *tmax, const int32_t *skip, int64_t n,
                                 int32_t *out_prim, float *out_t);
-/* vMF mixture: pdf at directions given identical parameters (mu K x d,
-   kappa K, lambda K per row) and one guided sample per row from Philox
+/* vMF mixture: pdf at directions given identical parameters (K = 1..16
+   lobes: mu K x d, kappa K, lambda K per row) and one guided sample per row from Philox
    counters (point, walk, step) with the walk's key; all host arrays. */
 wost_status wost_mixture_eval(int32_t dim, int32_t K, const float *mu, const float *kappa,
                               const float *lambda, const float *nu, int64_t n, float *out_pdf);

@@ -308,6 +308,10 @@ wost_status validate(int32_t njobs, const wost_job *jobs, int32_t guided, const 
         if (guided) {
             if (!J.field) { set_error(at + "a guided batch needs a field per job"); return WOST_ERR_INVALID_ARG; }
             if (J.field->desc.dim != dim) { set_error(at + "field dimension differs from the scene"); return WOST_ERR_INVALID_ARG; }
+            if (J.field->km != kMaxK) {
+                set_error(at + "many-scene launches decode fields of at most 8 lobes");
+                return WOST_ERR_UNSUPPORTED;
+            }
             if (wost_status dc = check_device(J.field->device, "wost_batch_create (field)")) return dc;
             if (ex.train && !fields.insert(J.field).second) {
                 set_error(at + "jobs that train need distinct fields");

@@ -171,8 +171,8 @@ extern "C" wost_status wost_create_field(const wost_field_desc *desc, wost_field
     if (!desc || !out) { set_error("wost_create_field: null argument"); return WOST_ERR_INVALID_ARG; }
     *out = nullptr;
     const wost_field_desc &d = *desc;
-    if ((d.dim != 2 && d.dim != 3) || d.K < 1 || d.K > kMaxK || d.levels != 16 || d.features != 2 || d.hidden != 64) {
-        set_error("wost_create_field: this library supports dim 2/3, K = 1..8, L = 16, F = 2, H = 64");
+    if ((d.dim != 2 && d.dim != 3) || d.K < 1 || d.K > kMaxKWide || d.levels != 16 || d.features != 2 || d.hidden != 64) {
+        set_error("wost_create_field: this library supports dim 2/3, K = 1..16, L = 16, F = 2, H = 64");
         return WOST_ERR_UNSUPPORTED;
     }
     if (d.log2_table < 8 || d.log2_table > 24 || d.base_res < 2 || d.max_res < d.base_res ||
@@ -188,6 +188,7 @@ extern "C" wost_status wost_create_field(const wost_field_desc *desc, wost_field
     f->desc = d;
     f->device = dev;
     f->nout = (d.dim + 2) * d.K + 1;
+    f->km = field_km(d.K);
     f->T = (int64_t)1 << d.log2_table;
     double b = d.levels > 1 ? std::exp((std::log((double)d.max_res) - std::log((double)d.base_res)) / (d.levels - 1)) : 1.0;
     // level l's entries start at level_off[l]: l 2^log2T in the hash grid;
@@ -212,8 +213,8 @@ extern "C" wost_status wost_create_field(const wost_field_desc *desc, wost_field
     void **mbufs[] = {(void **)&f->mlp32, (void **)&f->mlp_m, (void **)&f->mlp_v, (void **)&f->mlp_g};
     for (void **p : mbufs) if (rc == WOST_OK) rc = alloc(p, nm * sizeof(float));
     if (rc == WOST_OK) rc = alloc((void **)&f->grid16, (ng / 2) * sizeof(__half2));
-    if (rc == WOST_OK) rc = alloc((void **)&f->wimg, kWImgBytes);
-    if (rc == WOST_OK) rc = alloc((void **)&f->b3pad, kOutPad * sizeof(float));
+    if (rc == WOST_OK) rc = alloc((void **)&f->wimg, wimg_bytes(f->km));
+    if (rc == WOST_OK) rc = alloc((void **)&f->b3pad, out_pad(f->km) * sizeof(float));
     if (rc == WOST_OK) rc = alloc((void **)&f->loss_acc, 3 * sizeof(double));
     if (rc != WOST_OK) { delete f; return rc; }
     std::vector<float> grid, mlp;
@@ -224,7 +225,7 @@ extern "C" wost_status wost_create_field(const wost_field_desc *desc, wost_field
     if (e == cudaSuccess) e = cudaMemset(f->grid_v, 0, ng * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(f->mlp_m, 0, nm * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(f->mlp_v, 0, nm * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemset(f->wimg, 0, kWImgBytes);
+    if (e == cudaSuccess) e = cudaMemset(f->wimg, 0, wimg_bytes(f->km));
     if (e == cudaSuccess) e = cudaMemset(f->loss_acc, 0, 3 * sizeof(double));
     if (e != cudaSuccess) { delete f; return cuda_status(e, "wost_create_field"); }
     if ((rc = refresh_inference_copy(f, 0)) != WOST_OK) { delete f; return rc; }

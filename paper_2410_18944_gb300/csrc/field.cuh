@@ -22,43 +22,54 @@ namespace wost {
 
 constexpr int kFeat = 32;     // L * F
 constexpr int kHid = 64;      // hidden width
-constexpr int kOutPad = 48;   // padded output width (33 in 2D, 41 in 3D)
 constexpr int kMaxLevels = 16;
+// Lobe capacity of the kernels' internal output layout (below): 8 for the
+// standard kernels (K = 1..8), 16 for the wide-mixture kernels (K = 9..16,
+// the lobe-count ablation of Sec. 6.3).
 constexpr int kMaxK = 8;
+constexpr int kMaxKWide = 16;
+__host__ __device__ constexpr int field_km(int K) { return K <= kMaxK ? kMaxK : kMaxKWide; }
+// padded output width of the internal layout of KM lobes: (d + 2) KM + 1
+// outputs (33 / 41 for KM = 8, 65 / 81 for KM = 16) rounded up to a
+// multiple of 16, the N granule of the layer-3 MMA
+__host__ __device__ constexpr int out_pad(int KM) { return KM <= kMaxK ? 48 : 96; }
+constexpr int kOutPad = out_pad(kMaxK);
 
 // bf16 weight image in shared memory (core-matrix tiles, rows = outputs)
 constexpr int kW1Bytes = kHid * kFeat * 2;       // 64 x 32
 constexpr int kW2Bytes = kHid * kHid * 2;        // 64 x 64
-constexpr int kW3Bytes = kOutPad * kHid * 2;     // 48 x 64
-constexpr int kWImgBytes = kW1Bytes + kW2Bytes + kW3Bytes;
+__host__ __device__ constexpr int w3_bytes(int KM) { return out_pad(KM) * kHid * 2; }   // 48 (96) x 64
+__host__ __device__ constexpr int wimg_bytes(int KM) { return kW1Bytes + kW2Bytes + w3_bytes(KM); }
+constexpr int kW3Bytes = w3_bytes(kMaxK);
+constexpr int kWImgBytes = wimg_bytes(kMaxK);
 
-// The kernels read decoded outputs in one internal layout of kMaxK lobes:
-// mu'_i (kMaxK x d), kappa'_i, lambda'_i (kMaxK each), c', zero padding to
-// kOutPad.  A field of K < kMaxK lobes keeps its exchange layout (K lobes,
+// The kernels read decoded outputs in one internal layout of KM lobes:
+// mu'_i (KM x d), kappa'_i, lambda'_i (KM each), c', zero padding to
+// out_pad(KM).  A field of K < KM lobes keeps its exchange layout (K lobes,
 // nout = (d + 2) K + 1 rows); lobes K.. of the internal layout are disabled:
 // zero weights and a lambda' bias of kOffLambda, so their mixture weight is
 // exactly zero and every gradient into them vanishes (each carries a factor
 // of the weight).  Internal row -> exchange row (-1: none) and back:
 constexpr float kOffLambda = -1.0e4f;
-__host__ __device__ inline int out_row_to_exchange(int r, int d, int K) {
-    if (r < kMaxK * d) { int i = r / d; return i < K ? i * d + r % d : -1; }
-    r -= kMaxK * d;
-    if (r < kMaxK) return r < K ? K * d + r : -1;                   // kappa'
-    r -= kMaxK;
-    if (r < kMaxK) return r < K ? K * d + K + r : -1;               // lambda'
-    return r == kMaxK ? K * (d + 2) : -1;                           // c', padding
+__host__ __device__ inline int out_row_to_exchange(int r, int d, int K, int KM = kMaxK) {
+    if (r < KM * d) { int i = r / d; return i < K ? i * d + r % d : -1; }
+    r -= KM * d;
+    if (r < KM) return r < K ? K * d + r : -1;                      // kappa'
+    r -= KM;
+    if (r < KM) return r < K ? K * d + K + r : -1;                  // lambda'
+    return r == KM ? K * (d + 2) : -1;                              // c', padding
 }
-__host__ __device__ inline int exchange_to_out_row(int e, int d, int K) {
+__host__ __device__ inline int exchange_to_out_row(int e, int d, int K, int KM = kMaxK) {
     if (e < K * d) return (e / d) * d + e % d;
     e -= K * d;
-    if (e < K) return kMaxK * d + e;
+    if (e < K) return KM * d + e;
     e -= K;
-    if (e < K) return kMaxK * d + kMaxK + e;
-    return kMaxK * (d + 2);
+    if (e < K) return KM * d + KM + e;
+    return KM * (d + 2);
 }
-__host__ __device__ inline bool is_off_lambda(int r, int d, int K) {
-    const int i = r - (kMaxK * d + kMaxK);
-    return i >= K && i < kMaxK;
+__host__ __device__ inline bool is_off_lambda(int r, int d, int K, int KM = kMaxK) {
+    const int i = r - (KM * d + KM);
+    return i >= K && i < KM;
 }
 
 struct DevField {
@@ -161,10 +172,12 @@ __device__ __forceinline__ void encode_row(const DevField &f, const float *x, ui
     }
 }
 
-// One 128-row tile: X (128 x 32) -> H1 -> H2 -> Y (128 x 48) in TMEM columns
-// [tcol, tcol + 64).  Called by all 128 threads of the tile; thread `row`
-// owns row `row`.  `issuer` issues the MMAs.  On return out[0..47] holds this
-// row's raw outputs (+ bias).  Returns false if a bounded wait timed out.
+// One 128-row tile: X (128 x 32) -> H1 -> H2 -> Y (128 x out_pad(KM)) in
+// TMEM columns [tcol, tcol + tile_tmem_cols(KM)).  Called by all 128 threads
+// of the tile; thread `row` owns row `row`.  `issuer` issues the MMAs.  On
+// return out[0..out_pad(KM)) holds this row's raw outputs (+ bias).  Returns
+// false if a bounded wait timed out.
+__host__ __device__ constexpr int tile_tmem_cols(int KM) { return out_pad(KM) <= 64 ? 64 : 128; }
 struct TileCtx {
     uint8_t *xtile;     // 128 x 32 bf16
     uint8_t *htile;     // 128 x 64 bf16
@@ -175,6 +188,7 @@ struct TileCtx {
     int bar_id;         // named barrier of the tile (128 threads)
 };
 
+template <int KM = kMaxK>
 __device__ __forceinline__ bool tile_mma_wait(TileCtx &t, bool issuer, int which, int *err) {
     // which: 0 = layer 1, 1 = layer 2, 2 = layer 3
     fence_async_smem();
@@ -184,7 +198,7 @@ __device__ __forceinline__ bool tile_mma_wait(TileCtx &t, bool issuer, int which
         tc_fence_after();
         if (which == 0) umma_gemm(t.tmem, t.xtile, 0, kFeat, t.w, 0, kFeat, kHid, kFeat, false);
         else if (which == 1) umma_gemm(t.tmem, t.htile, 0, kHid, t.w + kW1Bytes, 0, kHid, kHid, kHid, false);
-        else umma_gemm(t.tmem, t.htile, 0, kHid, t.w + kW1Bytes + kW2Bytes, 0, kHid, kOutPad, kHid, false);
+        else umma_gemm(t.tmem, t.htile, 0, kHid, t.w + kW1Bytes + kW2Bytes, 0, kHid, out_pad(KM), kHid, false);
         umma_commit(t.mbar);
     }
     bool ok = mbar_wait_bounded(t.mbar, t.phase);
@@ -218,26 +232,32 @@ __device__ __forceinline__ void hidden_epilogue(TileCtx &t, int row, float *keep
     }
 }
 
+template <int KM = kMaxK>
 __device__ __forceinline__ bool mlp_tile_forward(TileCtx &t, const DevField &f, int row, bool issuer, float *out,
                                                  int *err) {
-    if (!tile_mma_wait(t, issuer, 0, err)) return false;
+    constexpr int OUT = out_pad(KM);
+    if (!tile_mma_wait<KM>(t, issuer, 0, err)) return false;
     hidden_epilogue(t, row, nullptr);
-    if (!tile_mma_wait(t, issuer, 1, err)) return false;
+    if (!tile_mma_wait<KM>(t, issuer, 1, err)) return false;
     hidden_epilogue(t, row, nullptr);
-    if (!tile_mma_wait(t, issuer, 2, err)) return false;
+    if (!tile_mma_wait<KM>(t, issuer, 2, err)) return false;
 #pragma unroll
-    for (int c = 0; c < kOutPad; c += 16) {
+    for (int c = 0; c < OUT; c += 16) {
         tmem_ld16(lane_addr(t.tmem, row, c), out + c);
         tmem_ld_wait();
     }
 #pragma unroll
-    for (int i = 0; i < kOutPad; ++i) out[i] += __ldg(f.b3 + i);
+    for (int i = 0; i < OUT; ++i) out[i] += __ldg(f.b3 + i);
     return true;
 }
 
 // shared setup of a 256-thread CTA running two MLP tiles: weight image,
-// two X and two H tiles, two mbarriers, the TMEM base address
-constexpr int kCtaTilesSmem = kWImgBytes + 2 * (128 * kFeat * 2) + 2 * (128 * kHid * 2) + 64;
+// two X and two H tiles, two mbarriers, the TMEM base address (two tiles of
+// tile_tmem_cols(KM) columns)
+__host__ __device__ constexpr int cta_tiles_smem(int KM) {
+    return wimg_bytes(KM) + 2 * (128 * kFeat * 2) + 2 * (128 * kHid * 2) + 64;
+}
+constexpr int kCtaTilesSmem = cta_tiles_smem(kMaxK);
 
 struct CtaTiles {
     uint8_t *wimg, *xt, *ht;
@@ -245,22 +265,24 @@ struct CtaTiles {
     uint32_t *tptr;
 };
 
+template <int KM = kMaxK>
 __device__ __forceinline__ CtaTiles cta_tiles_setup(uint8_t *sm, const DevField &f) {
+    constexpr int kImg = wimg_bytes(KM);
     CtaTiles c;
     c.wimg = sm;
-    c.xt = sm + kWImgBytes;
+    c.xt = sm + kImg;
     c.ht = c.xt + 2 * (128 * kFeat * 2);
     c.mbar = reinterpret_cast<uint64_t *>(c.ht + 2 * (128 * kHid * 2));
     c.tptr = reinterpret_cast<uint32_t *>(c.mbar + 2);
     const int tid = threadIdx.x;
-    for (int i = tid; i < kWImgBytes / 16; i += blockDim.x)
+    for (int i = tid; i < kImg / 16; i += blockDim.x)
         reinterpret_cast<uint4 *>(c.wimg)[i] = __ldg(f.wimg + i);
     if (tid == 0) {
         mbar_init(&c.mbar[0], 1);
         mbar_init(&c.mbar[1], 1);
         fence_mbar_init();
     }
-    if (tid < 32) tmem_alloc(c.tptr, 128);
+    if (tid < 32) tmem_alloc(c.tptr, 2 * tile_tmem_cols(KM));
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -268,11 +290,12 @@ __device__ __forceinline__ CtaTiles cta_tiles_setup(uint8_t *sm, const DevField 
     return c;
 }
 
+template <int KM = kMaxK>
 __device__ __forceinline__ void cta_tiles_teardown(const CtaTiles &c) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (threadIdx.x < 32) tmem_dealloc(*c.tptr, 128);
+    if (threadIdx.x < 32) tmem_dealloc(*c.tptr, 2 * tile_tmem_cols(KM));
 }
 
 }  // namespace wost
@@ -282,6 +305,7 @@ struct wost_field {
     wost_field_desc desc{};
     int device = -1;                         // CUDA device the field's buffers live on
     int nout = 0;
+    int km = wost::kMaxK;                    // lobe capacity of the kernels serving the field: field_km(K)
     int64_t T = 0;
     int res[16] = {0};
     uint32_t dense_mask = 0;

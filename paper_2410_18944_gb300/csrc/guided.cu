@@ -10,8 +10,10 @@
 namespace wost {
 
 constexpr int kGuidedBlock = 256;
-constexpr int kGuidedSmem = kCtaTilesSmem;
 constexpr int kWsSmem = ws_smem_bytes(false);
+// the 16-lobe kernel's tiles take this much more shared memory (weight image
+// and output region), which its scene staging gives up
+constexpr int kWsSmemWideExtra = ws_smem_bytes(false, kMaxKWide) - kWsSmem;
 
 struct GuidedArgs {
     WalkArgs w;
@@ -36,16 +38,18 @@ struct GuidedArgs {
 #define WOST_WS_WIDE_MB 64
 #endif
 
-template <int D, int W>
+// KM: lobe capacity of the field's output layout (8, or 16 for 9..16 lobes,
+// which run the standard walker count only)
+template <int D, int W, int KM = kMaxK>
 __global__ void __launch_bounds__(ws_threads(W), 1) guided_walk_kernel(const __grid_constant__ GuidedArgs g) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ DevScene staged;
     const DevScene *sc = &g.w.sc;
     if (g.stage_mask) {
-        stage_scene(g.w.sc, staged, reinterpret_cast<float4 *>(sm + kWsSmem), g.stage_mask);
+        stage_scene(g.w.sc, staged, reinterpret_cast<float4 *>(sm + ws_smem_bytes(false, KM)), g.stage_mask);
         sc = &staged;
     }
-    guided_ws_body<D, false, W>(SoloSrc<D>{g.w, &g.f, g.rd, sc}, g.o, sm);
+    guided_ws_body<D, false, W, KM>(SoloSrc<D>{g.w, &g.f, g.rd, sc}, g.o, sm);
 }
 
 // bytes of the scene's traversal data (the three BVHs' nodes and primitives
@@ -75,15 +79,22 @@ static int ws_walkers_for(const DevScene &s, int req, unsigned long long walks) 
 
 bool ws_walker_warps_valid(int w) { return w == 0 || w == kWsWalkerWarps || w == kWsWalkersWide; }
 
+// fields of 9..16 lobes run the standard walker count (the only 16-lobe
+// instantiation of the walk kernel)
+static int ws_walkers_for_field(const DevScene &s, const wost_field *f, int req, unsigned long long walks) {
+    return f->km == kMaxK ? ws_walkers_for(s, req, walks) : kWsWalkerWarps;
+}
+
 // decode of arbitrary points: the same tile forward as inside the walk
-template <int D>
+// (KM: lobe capacity of the field's internal output layout)
+template <int D, int KM>
 __global__ void __launch_bounds__(kGuidedBlock, 1) decode_kernel(DevField f, const double *pts, int64_t n,
                                                                  float *out, int nout, int *err) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    CtaTiles ct = cta_tiles_setup(sm, f);
+    CtaTiles ct = cta_tiles_setup<KM>(sm, f);
     const int tid = threadIdx.x, tile = tid >> 7, row = tid & 127;
     TileCtx t{ct.xt + tile * kXTileBytes, ct.ht + tile * kHTileBytes, ct.wimg, &ct.mbar[tile],
-              *ct.tptr + (uint32_t)(tile * 64), 0u, 1 + tile};
+              *ct.tptr + (uint32_t)(tile * tile_tmem_cols(KM)), 0u, 1 + tile};
     for (int64_t base = (int64_t)blockIdx.x * kGuidedBlock; base < n; base += (int64_t)gridDim.x * kGuidedBlock) {
         int64_t i = base + tid;
         float x[D];
@@ -93,22 +104,23 @@ __global__ void __launch_bounds__(kGuidedBlock, 1) decode_kernel(DevField f, con
         } else {
             zero_row(t.xtile, row, kFeat);
         }
-        float raw[kOutPad];
-        if (!mlp_tile_forward(t, f, row, row == 0, raw, err)) break;
+        float raw[out_pad(KM)];
+        if (!mlp_tile_forward<KM>(t, f, row, row == 0, raw, err)) break;
         if (i < n)
-            for (int k = 0; k < nout; ++k) out[i * nout + k] = raw[exchange_to_out_row(k, D, f.K)];
+            for (int k = 0; k < nout; ++k) out[i * nout + k] = raw[exchange_to_out_row(k, D, f.K, KM)];
     }
-    cta_tiles_teardown(ct);
+    cta_tiles_teardown<KM>(ct);
 }
 
-// mixture pdf / samples for given (normalised) parameters
-template <int D>
+// mixture pdf / samples for given (normalised) parameters: K <= KC lobes,
+// the remaining KC - K with weight 0
+template <int D, int KC>
 __global__ void mixture_eval_kernel(int K, const float *mu, const float *kap, const float *lam, const float *nu,
                                     int64_t n, float *out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    Mixture<D> m;
-    for (int j = 0; j < 8; ++j) {
+    Mixture<D, KC> m;
+    for (int j = 0; j < KC; ++j) {
         bool on = j < K;
         for (int k = 0; k < D; ++k) m.mu[j * D + k] = on ? mu[(i * K + j) * D + k] : 0.f;
         m.kappa[j] = on ? kap[i * K + j] : 1.f;
@@ -117,17 +129,17 @@ __global__ void mixture_eval_kernel(int K, const float *mu, const float *kap, co
     }
     float v[D];
     for (int k = 0; k < D; ++k) v[k] = nu[i * D + k];
-    out[i] = mixture_pdf<D, 8>(m, v);
+    out[i] = mixture_pdf<D, KC>(m, v);
 }
 
-template <int D>
+template <int D, int KC>
 __global__ void mixture_sample_kernel(int K, const float *mu, const float *kap, const float *lam,
                                       const uint32_t *ctr, uint32_t k0, uint32_t k1, int64_t n, float *onu,
                                       float *opdf) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    Mixture<D> m;
-    for (int j = 0; j < 8; ++j) {
+    Mixture<D, KC> m;
+    for (int j = 0; j < KC; ++j) {
         bool on = j < K;
         for (int k = 0; k < D; ++k) m.mu[j * D + k] = on ? mu[(i * K + j) * D + k] : 0.f;
         m.kappa[j] = on ? kap[i * K + j] : 1.f;
@@ -135,9 +147,9 @@ __global__ void mixture_sample_kernel(int K, const float *mu, const float *kap, 
         m.lognorm[j] = vmf_lognorm<D>(m.kappa[j]);
     }
     float v[D];
-    sample_direction<D, 8>(m, 1.f, ctr[3 * i], ctr[3 * i + 1], ctr[3 * i + 2], k0, k1, v);
+    sample_direction<D, KC>(m, 1.f, ctr[3 * i], ctr[3 * i + 1], ctr[3 * i + 2], k0, k1, v);
     for (int k = 0; k < D; ++k) onu[i * D + k] = v[k];
-    opdf[i] = mixture_pdf<D, 8>(m, v);
+    opdf[i] = mixture_pdf<D, KC>(m, v);
 }
 
 wost_status train_launch(wost_field *f, int dim, cudaStream_t st, bool apply_adam, float *loss_out_dev,
@@ -161,15 +173,19 @@ static int stage_budget_bytes() {
         int dev = 0, optin = 0;
         cudaFuncAttributes f2{}, f3{};
         cudaFuncAttributes w2{}, w3{};
+        cudaFuncAttributes k2{}, k3{};
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
             cudaFuncGetAttributes(&f2, guided_walk_kernel<2, kWsWalkerWarps>) != cudaSuccess ||
             cudaFuncGetAttributes(&f3, guided_walk_kernel<3, kWsWalkerWarps>) != cudaSuccess ||
             cudaFuncGetAttributes(&w2, guided_walk_kernel<2, kWsWalkersWide>) != cudaSuccess ||
-            cudaFuncGetAttributes(&w3, guided_walk_kernel<3, kWsWalkersWide>) != cudaSuccess)
+            cudaFuncGetAttributes(&w3, guided_walk_kernel<3, kWsWalkersWide>) != cudaSuccess ||
+            cudaFuncGetAttributes(&k2, guided_walk_kernel<2, kWsWalkerWarps, kMaxKWide>) != cudaSuccess ||
+            cudaFuncGetAttributes(&k3, guided_walk_kernel<3, kWsWalkerWarps, kMaxKWide>) != cudaSuccess)
             return 0;
-        const int stat = (int)std::max(std::max(f2.sharedSizeBytes, f3.sharedSizeBytes),
-                                       std::max(w2.sharedSizeBytes, w3.sharedSizeBytes));
+        const int stat = (int)std::max(std::max(std::max(f2.sharedSizeBytes, f3.sharedSizeBytes),
+                                                std::max(w2.sharedSizeBytes, w3.sharedSizeBytes)),
+                                       std::max(k2.sharedSizeBytes, k3.sharedSizeBytes));
         budget = std::max(0, std::min(optin - kWsSmem - stat - 1024, WOST_STAGE_MAX_KB * 1024));
     }
     return budget;
@@ -180,12 +196,17 @@ wost_status guided_occupancy(int dim, int *per_sm) {
     if (!set[dim]) {
         const int bytes = kWsSmem + stage_budget_bytes();
         const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        // (the 16-lobe kernel stages less of the scene: the same total)
         if (dim == 2) {
             WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<2, kWsWalkerWarps>, at, bytes));
             WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<2, kWsWalkersWide>, at, bytes));
+            WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<2, kWsWalkerWarps, kMaxKWide>, at,
+                                           std::max(bytes, ws_smem_bytes(false, kMaxKWide))));
         } else {
             WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<3, kWsWalkerWarps>, at, bytes));
             WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<3, kWsWalkersWide>, at, bytes));
+            WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<3, kWsWalkerWarps, kMaxKWide>, at,
+                                           std::max(bytes, ws_smem_bytes(false, kMaxKWide))));
         }
         set[dim] = true;
     }
@@ -193,17 +214,26 @@ wost_status guided_occupancy(int dim, int *per_sm) {
     return WOST_OK;
 }
 
-// regions of the scene to stage, and their size in float4
-static int stage_mask_for(const DevScene &sc, int *f4) {
-    return stage_plan(sc, stage_budget_bytes() / 16, f4);
+// regions of the scene to stage, and their size in float4 (km: lobe
+// capacity of the launch's kernel)
+static int stage_mask_for(const DevScene &sc, int *f4, int km = kMaxK) {
+    const int budget = stage_budget_bytes() - (km == kMaxK ? 0 : kWsSmemWideExtra);
+    return stage_plan(sc, std::max(budget, 0) / 16, f4);
 }
 
-wost_status launch_guided(int dim, const GuidedArgs &g, int grid, cudaStream_t st, int walkers) {
+wost_status launch_guided(int dim, const GuidedArgs &g, int grid, cudaStream_t st, int walkers, int km = kMaxK) {
     int f4 = 0;
-    stage_mask_for(g.w.sc, &f4);
+    stage_mask_for(g.w.sc, &f4, km);
+    constexpr int tn = ws_threads(kWsWalkerWarps), tw = ws_threads(kWsWalkersWide);
+    if (km != kMaxK) {
+        const int smem16 = ws_smem_bytes(false, kMaxKWide) + f4 * 16;
+        if (dim == 2) guided_walk_kernel<2, kWsWalkerWarps, kMaxKWide><<<grid, tn, smem16, st>>>(g);
+        else guided_walk_kernel<3, kWsWalkerWarps, kMaxKWide><<<grid, tn, smem16, st>>>(g);
+        WOST_CUDA(cudaGetLastError());
+        return WOST_OK;
+    }
     const int smem = kWsSmem + f4 * 16;
     const bool wide = walkers == kWsWalkersWide;
-    constexpr int tn = ws_threads(kWsWalkerWarps), tw = ws_threads(kWsWalkersWide);
     if (dim == 2 && wide) guided_walk_kernel<2, kWsWalkersWide><<<grid, tw, smem, st>>>(g);
     else if (dim == 2) guided_walk_kernel<2, kWsWalkerWarps><<<grid, tn, smem, st>>>(g);
     else if (wide) guided_walk_kernel<3, kWsWalkersWide><<<grid, tw, smem, st>>>(g);
@@ -223,11 +253,22 @@ constexpr int kWfMaxSlots = 1 << 20;
 wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, const wost_exec &ex,
                          cudaStream_t st, wost_stats *stats, int walk_begin, CallTiming &tm) {
     if (f->desc.dim != s->dim) { set_error("wost_solve: field dimension differs from the scene"); return WOST_ERR_INVALID_ARG; }
+    // fields of 9..16 lobes: the 16-lobe warp-specialised kernel serves every
+    // launch (the wavefront path decodes 8-lobe layouts only)
+    const bool wide_mix = f->km != kMaxK;
+    if (wide_mix && ex.guided_kernel == 2) {
+        set_error("wost_solve: the wavefront kernel serves fields of at most 8 lobes");
+        return WOST_ERR_UNSUPPORTED;
+    }
+    if (wide_mix && ex.walker_warps != 0 && ex.walker_warps != kWsWalkerWarps) {
+        set_error("wost_solve: fields of more than 8 lobes run the standard walker count");
+        return WOST_ERR_UNSUPPORTED;
+    }
     GuidedArgs g{};
     g.f = f->dev();
     {
         int f4 = 0;
-        g.stage_mask = stage_mask_for(s->dev, &f4);
+        g.stage_mask = stage_mask_for(s->dev, &f4, f->km);
     }
     g.o.c_mode = ex.c_mode;
     g.o.c_fixed = ex.c_fixed;
@@ -246,8 +287,8 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
     // kernel serves that best.  Launches without records run every walk at
     // once, and the wavefront keeps its slots full of them.
     const int rounds = ex.train ? std::max(0, std::min(nwalks, ex.train_until_wpp - walk_begin)) : 0;
-    const bool wavefront = ex.guided_kernel == 2 || (ex.guided_kernel == 0 && rounds == 0);
-    const bool ws_then_wavefront = ex.guided_kernel == 0 && rounds > 0 && rounds < nwalks;
+    const bool wavefront = !wide_mix && (ex.guided_kernel == 2 || (ex.guided_kernel == 0 && rounds == 0));
+    const bool ws_then_wavefront = !wide_mix && ex.guided_kernel == 0 && rounds > 0 && rounds < nwalks;
     // walks per point in one training batch (the last one clipped at `rounds`)
     const int bwpp = std::max(1, std::min(ex.batch_wpp, std::max(rounds, 1)));
     int ntrain = 0;
@@ -315,8 +356,8 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
         int cps = ex.ctas_per_sm > 0 ? std::min(ex.ctas_per_sm, occ) : occ;
         int grid = num_sms() * cps;
         // the largest launch of the solve: a training batch, or one walk per point
-        const int walkers = ws_walkers_for(s->dev, ex.walker_warps,
-                                           (unsigned long long)a.npoints * (unsigned long long)(rounds > 0 ? bwpp : 1));
+        const int walkers = ws_walkers_for_field(s->dev, f, ex.walker_warps,
+                                                 (unsigned long long)a.npoints * (unsigned long long)(rounds > 0 ? bwpp : 1));
         if (rounds > 0) {
             size_t scratch = (size_t)grid * (walkers * 32) * (size_t)std::max(a.maxsteps, 1) * kRecFloats *
                              sizeof(float);
@@ -338,7 +379,7 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
             WOST_CUDA(cudaMemsetAsync(a.work_ctr, 0, sizeof(unsigned long long), st));
             if (g.o.record) WOST_CUDA(cudaMemsetAsync(f->rec_ctr, 0, 2 * sizeof(unsigned long long), st));
             tm.mark(tm.walk, st);
-            wost_status rc = launch_guided(s->dim, g, grid, st, walkers);
+            wost_status rc = launch_guided(s->dim, g, grid, st, walkers, f->km);
             tm.mark(tm.walk, st);
             tm.launches++;
             tm.walk_launches++;
@@ -389,13 +430,16 @@ extern "C" wost_status wost_field_decode(wost_field *f, const double *points, in
         own_o = true;
     }
     int grid = (int)std::min<int64_t>((n + kGuidedBlock - 1) / kGuidedBlock, (int64_t)num_sms() * 2);
-    if (D == 2) {
-        WOST_CUDA(cudaFuncSetAttribute(decode_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGuidedSmem));
-        decode_kernel<2><<<grid, kGuidedBlock, kGuidedSmem, st>>>(f->dev(), dp, n, dout, f->nout, device_err_flag());
-    } else {
-        WOST_CUDA(cudaFuncSetAttribute(decode_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGuidedSmem));
-        decode_kernel<3><<<grid, kGuidedBlock, kGuidedSmem, st>>>(f->dev(), dp, n, dout, f->nout, device_err_flag());
-    }
+    auto launch = [&](auto kern, int smem) -> wost_status {
+        WOST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        kern<<<grid, kGuidedBlock, smem, st>>>(f->dev(), dp, n, dout, f->nout, device_err_flag());
+        return WOST_OK;
+    };
+    constexpr int s8 = cta_tiles_smem(kMaxK), s16 = cta_tiles_smem(kMaxKWide);
+    wost_status lrc = f->km == kMaxK ? (D == 2 ? launch(decode_kernel<2, kMaxK>, s8) : launch(decode_kernel<3, kMaxK>, s8))
+                                     : (D == 2 ? launch(decode_kernel<2, kMaxKWide>, s16)
+                                               : launch(decode_kernel<3, kMaxKWide>, s16));
+    if (lrc != WOST_OK) return lrc;
     WOST_CUDA(cudaGetLastError());
     if (own_o) WOST_CUDA(cudaMemcpyAsync(out_raw, dout, n * f->nout * sizeof(float), cudaMemcpyDeviceToHost, st));
     WOST_CUDA(cudaStreamSynchronize(st));
@@ -407,7 +451,7 @@ extern "C" wost_status wost_field_decode(wost_field *f, const double *points, in
 namespace {
 wost_status mixture_common(int dim, int K, int64_t n, const float *mu, const float *kappa, const float *lambda,
                            float **dmu, float **dk, float **dl) {
-    if ((dim != 2 && dim != 3) || K < 1 || K > 8 || n < 0 || (n > 0 && (!mu || !kappa || !lambda))) {
+    if ((dim != 2 && dim != 3) || K < 1 || K > kMaxKWide || n < 0 || (n > 0 && (!mu || !kappa || !lambda))) {
         set_error("wost_mixture: invalid argument");
         return WOST_ERR_INVALID_ARG;
     }
@@ -432,8 +476,11 @@ extern "C" wost_status wost_mixture_eval(int32_t dim, int32_t K, const float *mu
     if (e == cudaSuccess) e = cudaMemcpy(dn, nu, n * dim * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         int bs = 128, gr = (int)((n + bs - 1) / bs);
-        if (dim == 2) mixture_eval_kernel<2><<<gr, bs>>>(K, dmu, dk, dl, dn, n, dout);
-        else mixture_eval_kernel<3><<<gr, bs>>>(K, dmu, dk, dl, dn, n, dout);
+        const bool wide = K > kMaxK;
+        if (dim == 2 && !wide) mixture_eval_kernel<2, kMaxK><<<gr, bs>>>(K, dmu, dk, dl, dn, n, dout);
+        else if (dim == 2) mixture_eval_kernel<2, kMaxKWide><<<gr, bs>>>(K, dmu, dk, dl, dn, n, dout);
+        else if (!wide) mixture_eval_kernel<3, kMaxK><<<gr, bs>>>(K, dmu, dk, dl, dn, n, dout);
+        else mixture_eval_kernel<3, kMaxKWide><<<gr, bs>>>(K, dmu, dk, dl, dn, n, dout);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(out_pdf, dout, n * sizeof(float), cudaMemcpyDeviceToHost);
@@ -456,8 +503,11 @@ extern "C" wost_status wost_mixture_sample(int32_t dim, int32_t K, const float *
     if (e == cudaSuccess) {
         int bs = 128, gr = (int)((n + bs - 1) / bs);
         uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32) + scene_id;
-        if (dim == 2) mixture_sample_kernel<2><<<gr, bs>>>(K, dmu, dk, dl, dc, k0, k1, n, dnu, dpdf);
-        else mixture_sample_kernel<3><<<gr, bs>>>(K, dmu, dk, dl, dc, k0, k1, n, dnu, dpdf);
+        const bool wide = K > kMaxK;
+        if (dim == 2 && !wide) mixture_sample_kernel<2, kMaxK><<<gr, bs>>>(K, dmu, dk, dl, dc, k0, k1, n, dnu, dpdf);
+        else if (dim == 2) mixture_sample_kernel<2, kMaxKWide><<<gr, bs>>>(K, dmu, dk, dl, dc, k0, k1, n, dnu, dpdf);
+        else if (!wide) mixture_sample_kernel<3, kMaxK><<<gr, bs>>>(K, dmu, dk, dl, dc, k0, k1, n, dnu, dpdf);
+        else mixture_sample_kernel<3, kMaxKWide><<<gr, bs>>>(K, dmu, dk, dl, dc, k0, k1, n, dnu, dpdf);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(out_nu, dnu, n * dim * sizeof(float), cudaMemcpyDeviceToHost);

@@ -79,15 +79,23 @@ constexpr int kWsThreads = ws_threads(kWsWalkerWarps);
 // waits for the tile in flight, so tiles fill fuller and the shared memory
 // the buffers do not take goes to the scene and to L1.
 constexpr int kNT = WOST_WS_TILES;
-constexpr uint32_t kWsTmemCols = tmem_cols(kNT * 64);   // allocation rounded up to a power of two
-static_assert(kNT >= 1 && kNT * 64 <= 512, "decode tile buffers must fit in the 512 TMEM columns");
+// TMEM columns of a decode buffer: the 64 hidden columns, or the 96 outputs
+// of a 16-lobe layout
+__host__ __device__ constexpr int ws_buf_cols(int KM) { return tile_tmem_cols(KM); }
+// allocation rounded up to a power of two
+__host__ __device__ constexpr uint32_t ws_tmem_cols(int KM) { return tmem_cols(kNT * ws_buf_cols(KM)); }
+static_assert(kNT >= 1 && kNT * ws_buf_cols(kMaxKWide) <= 512, "decode tile buffers must fit in the 512 TMEM columns");
 // The `full` and `done` barriers of a buffer can never run two phases ahead
 // of their waiters: a tile's quarters arrive only after the tile kNT earlier
 // is consumed, which follows its `done`, which follows its `full`.
 constexpr int kXTileBytes = 128 * kFeat * 2;
 constexpr int kHTileBytes = 128 * kHid * 2;
-constexpr int kYStride = 50;                 // FP16 output row stride (25 words: conflict-free)
-constexpr int kYBytes = 128 * kYStride * 2;  // aliases the hidden tile once layer 3 has run
+// FP16 output row stride: an odd number of words, so the 32 rows of a warp
+// fall in distinct banks (50 halves for 48 outputs, 98 for 96)
+__host__ __device__ constexpr int ws_y_stride(int KM) { return out_pad(KM) + 2; }
+__host__ __device__ constexpr int ws_y_bytes(int KM) { return 128 * ws_y_stride(KM) * 2; }
+constexpr int kYStride = ws_y_stride(kMaxK);
+constexpr int kYBytes = ws_y_bytes(kMaxK);   // aliases the hidden tile once layer 3 has run
 static_assert(kYBytes <= kHTileBytes, "decoded outputs must fit in the hidden-activation tile");
 constexpr int kBufBytes = kXTileBytes + kHTileBytes;
 constexpr int kWsCtrlBytes = 512;
@@ -95,10 +103,12 @@ constexpr int kWSlots = 2;                   // weight images cached by a multi-
 constexpr int ws_weight_slots(bool multi) { return multi ? kWSlots : 1; }
 // Multi-scene CTAs keep the decoded outputs in a region of their own: a
 // later pass writes hidden activations of its rows in the core-matrix
-// layout, which spans the bytes of other rows' row-major outputs.
-constexpr int ws_smem_bytes(bool multi) {
-    return kWImgBytes * ws_weight_slots(multi) + kNT * kBufBytes + kWsCtrlBytes +
-           (multi ? kNT * (128 * 4 + kYBytes) : 0);
+// layout, which spans the bytes of other rows' row-major outputs.  So do
+// 16-lobe layouts, whose 96 outputs exceed the hidden tile.
+__host__ __device__ constexpr bool ws_y_separate(bool multi, int KM) { return multi || KM > kMaxK; }
+__host__ __device__ constexpr int ws_smem_bytes(bool multi, int KM = kMaxK) {
+    return wimg_bytes(KM) * ws_weight_slots(multi) + kNT * kBufBytes + kWsCtrlBytes + (multi ? kNT * 128 * 4 : 0) +
+           (ws_y_separate(multi, KM) ? kNT * ws_y_bytes(KM) : 0);
 }
 // Server polls before closing a partial tile.  Fuller tiles measured faster
 // (one GB300, training batches: icosphere 374 / 364 / 354 / 339-347 / 335 ms
@@ -197,27 +207,34 @@ __device__ __forceinline__ void end_recorded_walk(const RecDest &rd, const float
 }
 
 // W walker warps (a template parameter: launches over scenes whose traversal
-// data misses L2 take more walkers to hide its latency)
-template <int D, bool kMulti, int W = kWsWalkerWarps, class Src>
+// data misses L2 take more walkers to hide its latency); KM: lobe capacity of
+// the decoded output layout (8, or 16 for fields of 9..16 lobes; single-scene
+// launches only)
+template <int D, bool kMulti, int W = kWsWalkerWarps, int KM = kMaxK, class Src>
 __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, uint8_t *sm) {
+    static_assert(!kMulti || KM == kMaxK, "multi-scene launches decode 8-lobe layouts");
     constexpr int kThreads = ws_threads(W);
     constexpr int kSlots = ws_weight_slots(kMulti);
+    constexpr int kImg = wimg_bytes(KM), OUT = out_pad(KM), YS = ws_y_stride(KM);
+    constexpr uint32_t kTmemCols = ws_tmem_cols(KM);
     uint8_t *wslots = sm;
-    uint8_t *bufs = sm + kSlots * kWImgBytes;
+    uint8_t *bufs = sm + kSlots * kImg;
     WsCtrl *ctl = reinterpret_cast<WsCtrl *>(bufs + kNT * kBufBytes);
     int *rowjob = reinterpret_cast<int *>(bufs + kNT * kBufBytes + kWsCtrlBytes);   // [kNT][128], multi only
-    uint8_t *ybufs = bufs + kNT * kBufBytes + kWsCtrlBytes + kNT * 128 * 4;          // multi only
+    // separate output region (multi-scene or 16-lobe layouts)
+    uint8_t *ybufs = bufs + kNT * kBufBytes + kWsCtrlBytes + (kMulti ? kNT * 128 * 4 : 0);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     auto Xb = [&](int b) { return bufs + b * kBufBytes; };
     auto Hb = [&](int b) { return bufs + b * kBufBytes + kXTileBytes; };
     // decoded raw outputs (FP16): one pass per tile overwrites the hidden
     // tile after the last MMA read it; several passes use their own region
     auto Yb = [&](int b) {
-        return reinterpret_cast<__half *>(kMulti ? ybufs + b * kYBytes : bufs + b * kBufBytes + kXTileBytes);
+        return reinterpret_cast<__half *>(ws_y_separate(kMulti, KM) ? ybufs + b * ws_y_bytes(KM)
+                                                                    : bufs + b * kBufBytes + kXTileBytes);
     };
 
     if (!kMulti)
-        for (int i = tid; i < kWImgBytes / 16; i += kThreads)
+        for (int i = tid; i < kImg / 16; i += kThreads)
             reinterpret_cast<uint4 *>(wslots)[i] = __ldg(src.wimg(0) + i);
     if (tid == 0) {
         for (int b = 0; b < kNT; ++b) {
@@ -232,7 +249,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
         for (int i = 0; i < kWSlots; ++i) ctl->wtag[i] = -1;
         fence_mbar_init();
     }
-    if (warp == 0) tmem_alloc(&ctl->tmem, kWsTmemCols);
+    if (warp == 0) tmem_alloc(&ctl->tmem, kTmemCols);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -289,7 +306,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
             const int go = ctl->go, pad = ctl->padmask;
             named_sync(1, 128);
             if (go <= 0) break;
-            const uint32_t tm = tmem0 + (uint32_t)(b * 64);
+            const uint32_t tm = tmem0 + (uint32_t)(b * ws_buf_cols(KM));
             const int rj = kMulti ? rowjob[b * 128 + row] : 0;   // -1: padding row
             bool pending = rj >= 0;
             bool ok = true;
@@ -313,8 +330,8 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
                         s = ctl->wnext;
                         named_sync(1, 128);
                         const uint4 *src_w = src.wimg(pj);
-                        uint4 *dst = reinterpret_cast<uint4 *>(wslots + s * kWImgBytes);
-                        for (int i = tid; i < kWImgBytes / 16; i += 128) dst[i] = __ldg(src_w + i);
+                        uint4 *dst = reinterpret_cast<uint4 *>(wslots + s * kImg);
+                        for (int i = tid; i < kImg / 16; i += 128) dst[i] = __ldg(src_w + i);
                         fence_async_smem();
                         if (tid == 0) {
                             ctl->wtag[s] = pj;
@@ -322,19 +339,19 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
                         }
                         named_sync(1, 128);
                     }
-                    wimg = wslots + s * kWImgBytes;
+                    wimg = wslots + s * kImg;
                 }
                 // this thread's row takes the pass; tcgen05.ld is warp-collective,
                 // so a warp loads when any of its rows does
                 const bool mine = !kMulti || rj == pj;
                 const bool warp_mine = !kMulti || __any_sync(0xffffffffu, mine);
-                // three layers: X -> H -> H -> Y (TMEM columns [b*64, b*64 + 64))
+                // three layers: X -> H -> H -> Y (TMEM columns [tm, tm + ws_buf_cols(KM)))
                 for (int layer = 0; layer < 3 && ok; ++layer) {
                     if (tid == 0) {
                         tc_fence_after();
                         if (layer == 0) umma_gemm(tm, Xb(b), 0, kFeat, wimg, 0, kFeat, kHid, kFeat, false);
                         else if (layer == 1) umma_gemm(tm, Hb(b), 0, kHid, wimg + kW1Bytes, 0, kHid, kHid, kHid, false);
-                        else umma_gemm(tm, Hb(b), 0, kHid, wimg + kW1Bytes + kW2Bytes, 0, kHid, kOutPad, kHid, false);
+                        else umma_gemm(tm, Hb(b), 0, kHid, wimg + kW1Bytes + kW2Bytes, 0, kHid, OUT, kHid, false);
                         umma_commit(&ctl->mma);
                     }
                     ok = mbar_wait_bounded(&ctl->mma, mma_phase);
@@ -361,11 +378,11 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
                         named_sync(1, 128);
                     } else {
                         // the layer-3 MMA has completed: its H operand is dead, so
-                        // (one pass) the FP16 outputs can take its place
+                        // (one pass, 8 lobes) the FP16 outputs can take its place
                         if (warp_mine) {
                             const float *b3 = src.b3(pj);
-                            __half *y = Yb(b) + row * kYStride;
-                            for (int c = 0; c < kOutPad; c += 16) {
+                            __half *y = Yb(b) + row * YS;
+                            for (int c = 0; c < OUT; c += 16) {
                                 float v[16];
                                 tmem_ld16(lane_addr(tm, row, c), v);
                                 tmem_ld_wait();
@@ -456,11 +473,11 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
             bool zero_density = false;
             float wgt = 1.f, ptil = 0.f;
             if (live) {
-                RowMixture<D, 8> m;
-                m.init(Yb(b) + row * kYStride);
+                RowMixture<D, KM> m;
+                m.init(Yb(b) + row * YS);
                 const float c = o.c_mode ? o.c_fixed : m.c();
                 const StepEnv env = src.env(w);
-                bool from_guide = sample_direction_row<D, 8>(m, c, w.pid, w.wid, (uint32_t)w.k, env.key0, env.key1, nu);
+                bool from_guide = sample_direction_row<D, KM>(m, c, w.pid, w.wid, (uint32_t)w.k, env.key0, env.key1, nu);
                 const bool onN = w.prim >= 0;
                 if (onN) {
                     float dn = dotv<D>(nu, w.n);
@@ -515,7 +532,7 @@ __device__ __forceinline__ void guided_ws_body(const Src &src, const WsOpts &o, 
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem0, kWsTmemCols);
+    if (warp == 0) tmem_dealloc(tmem0, kTmemCols);
 }
 
 }  // namespace wost

@@ -16,6 +16,7 @@
 //   are flushed once with atomics.  Activations are recomputed, not stored.
 // Then one elementwise Adam kernel (Kingma & Ba 2015) updates the FP32
 // masters and rewrites the FP16 grid and BF16 weight-image copies.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -25,16 +26,31 @@
 
 namespace wost {
 
-constexpr int kTrainBlock = 256;
+// Per KM (lobe capacity of the field's output layout, 8 or 16):
 constexpr int kTX = 128 * kFeat * 2;     // X tile
 constexpr int kTH = 128 * kHid * 2;      // H1 / H2 tiles
-constexpr int kTG = 128 * 128 * 2;       // G tile: [dY | dZ2] then [dZ1 | dZ2]
+// G tile, gcols(KM) columns: [dY | 0 | dZ2] (dZ2 from column z2col(KM)),
+// then [dZ1 | ... | dZ2].  KM = 8: 48 + 16 + 64 = 128; KM = 16: 96 + 64 = 160
+__host__ __device__ constexpr int z2col(int KM) { return KM <= kMaxK ? 64 : 96; }
+__host__ __device__ constexpr int gcols(int KM) { return z2col(KM) + kHid; }
+__host__ __device__ constexpr int tg_bytes(int KM) { return 128 * gcols(KM) * 2; }
 // gradient tiles are stored as a BF16 pair hi + lo (lo = bf16(v - hi)), so the
 // MMAs see the FP32 gradient to ~16 bits; activations and weights are BF16
 // exactly as in the forward pass
-constexpr int kTileBytes = kTX + 2 * kTH + 2 * kTG;
+__host__ __device__ constexpr int tile_bytes(int KM) { return kTX + 2 * kTH + 2 * tg_bytes(KM); }
+// 128-record tiles per CTA: two for KM = 8 (226 KB of shared memory); one for
+// KM = 16, whose tile and TMEM columns (128 + 3 x 64) do not fit twice
+__host__ __device__ constexpr int train_tiles(int KM) { return KM <= kMaxK ? 2 : 1; }
+__host__ __device__ constexpr int train_block(int KM) { return 128 * train_tiles(KM); }
+// TMEM columns of the scratch accumulator s0 of a tile (the layer-3 outputs)
+__host__ __device__ constexpr int s0cols(int KM) { return tile_tmem_cols(KM); }
 constexpr int kTrainCtl = 128;   // mbarriers, TMEM address, per-level gradient copy offsets
-constexpr int kTrainSmem = kWImgBytes + 2 * kTileBytes + kTrainCtl;
+__host__ __device__ constexpr int train_smem(int KM) {
+    return wimg_bytes(KM) + train_tiles(KM) * tile_bytes(KM) + kTrainCtl;
+}
+static_assert(train_smem(kMaxK) <= 227 * 1024 && train_smem(kMaxKWide) <= 227 * 1024, "training tiles");
+static_assert(train_tiles(kMaxK) * (s0cols(kMaxK) + 3 * 64) <= 512 &&
+              train_tiles(kMaxKWide) * (s0cols(kMaxKWide) + 3 * 64) <= 512, "training TMEM columns");
 
 // Gradient copies of the coarse levels.  Every record scatters onto each
 // level, so the few hundred to few thousand vertices of a coarse level take
@@ -130,13 +146,14 @@ __device__ __forceinline__ void ld_cols(uint32_t taddr, int row, int ncols, floa
     }
 }
 
-// loss and gradient w.r.t. the raw outputs for one record
-template <int D>
+// loss and gradient w.r.t. the raw outputs (internal layout of KM lobes) for
+// one record
+template <int D, int KM>
 __device__ __forceinline__ float record_grad(const TrainArgs &a, const float *rec, const float *raw, float inv_n,
                                              float *draw) {
-    const int K = 8;
-    Mixture<D> m;
-    theta_map<D, 8>(raw, m);
+    constexpr int K = KM;
+    Mixture<D, KM> m;
+    theta_map<D, KM>(raw, m);
     const float c = a.c_mode ? a.c_fixed : m.c;
     float nu[2][3], nrm[3];
     for (int i = 0; i < 3; ++i) { nu[0][i] = rec[3 + i]; nrm[i] = rec[6 + i]; }
@@ -148,7 +165,7 @@ __device__ __forceinline__ float record_grad(const TrainArgs &a, const float *re
         for (int i = 0; i < D; ++i) nu[1][i] = nu[0][i] - t * nrm[i];
         nd = 2;
     }
-    float v[2][8], pg = 0.f;
+    float v[2][KM], pg = 0.f;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         float s = 0.f;
@@ -161,7 +178,7 @@ __device__ __forceinline__ float record_grad(const TrainArgs &a, const float *re
     const float area = D == 2 ? 2.f * WOST_PI : 4.f * WOST_PI;
     const float pu = (onN ? 2.f : 1.f) / area;
     const float ptil = c * pg + (1.f - c) * pu;
-    for (int i = 0; i < kOutPad; ++i) draw[i] = 0.f;
+    for (int i = 0; i < out_pad(KM); ++i) draw[i] = 0.f;
     if (!(pt > 0.f) || !(q > 0.f)) return 0.f;
     const float wt = pt / q;
     const float pgs = fmaxf(pg, 1e-30f);
@@ -193,28 +210,31 @@ __device__ __forceinline__ float record_grad(const TrainArgs &a, const float *re
     return loss;
 }
 
-template <int D>
-__global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
+template <int D, int KM>
+__global__ void __launch_bounds__(train_block(KM), 1) train_kernel(TrainArgs a) {
+    constexpr int TPC = train_tiles(KM), OUT = out_pad(KM), GC = gcols(KM), Z2 = z2col(KM), S0C = s0cols(KM);
+    constexpr int kImg = wimg_bytes(KM), kTileB = tile_bytes(KM);
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, tl = tid >> 7, row = tid & 127;
     const bool issuer = row == 0;
     uint8_t *wimg = sm;
-    uint8_t *tb = sm + kWImgBytes + tl * kTileBytes;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kWImgBytes + 2 * kTileBytes);
+    uint8_t *tb = sm + kImg + tl * kTileB;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kImg + TPC * kTileB);
     uint32_t *tptr = reinterpret_cast<uint32_t *>(mbar + 2);
     uint32_t *copy_off = tptr + 2;   // [kMaxLevels]: this CTA's gradient copy of each level (entries)
     if (tid < kMaxLevels)
         copy_off[tid] = tid < a.f.L ? (uint32_t)((blockIdx.x % a.gc.copy_R[tid]) * a.gc.copy_V[tid]) : 0u;
-    for (int i = tid; i < kWImgBytes / 16; i += kTrainBlock) reinterpret_cast<uint4 *>(wimg)[i] = __ldg(a.f.wimg + i);
+    for (int i = tid; i < kImg / 16; i += train_block(KM)) reinterpret_cast<uint4 *>(wimg)[i] = __ldg(a.f.wimg + i);
     if (tid == 0) { mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1); fence_mbar_init(); }
     if (tid < 32) tmem_alloc(tptr, 512);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tb0 = *tptr + (uint32_t)(tl * 256);
-    TTile t{tb, tb + kTX, tb + kTX + kTH, tb + kTX + 2 * kTH, tb + kTX + 2 * kTH + kTG, wimg, &mbar[tl],
-            tb0, tb0 + 64, tb0 + 128, tb0 + 192, 0u, 1 + tl};
+    // TMEM of a tile: s0 (S0C columns), then the accumulators of dW3, dW2, dW1
+    const uint32_t tb0 = *tptr + (uint32_t)(tl * (S0C + 3 * 64));
+    TTile t{tb, tb + kTX, tb + kTX + kTH, tb + kTX + 2 * kTH, tb + kTX + 2 * kTH + tg_bytes(KM), wimg, &mbar[tl],
+            tb0, tb0 + S0C, tb0 + S0C + 64, tb0 + S0C + 128, 0u, 1 + tl};
 
     // the records this step uses: all of them, or the stratum o, o + k, ...
     // of about max_samples records (k = ceil(n / max_samples), o from the
@@ -231,10 +251,10 @@ __global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
     const float inv_n = nrec > 0 ? 1.f / (float)nrec : 0.f;
     const long long ntiles = (nrec + 127) / 128;
     bool have_acc = false, ok = true;
-    float db3 = 0.f;      // column `row` (< kOutPad) of the bias gradient
+    float db3 = 0.f;      // column `row` (< OUT) of the bias gradient
     double loss_local = 0.0;
 
-    for (long long tile = (long long)blockIdx.x * 2 + tl; tile < ntiles && ok; tile += (long long)gridDim.x * 2) {
+    for (long long tile = (long long)blockIdx.x * TPC + tl; tile < ntiles && ok; tile += (long long)gridDim.x * TPC) {
         const long long ri = off + (tile * 128 + row) * kstride;
         const bool valid = tile * 128 + row < nrec;
         float rec[12];
@@ -267,37 +287,37 @@ __global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
             for (int i = 0; i < 8; ++i) v8[i] = fmaxf(h[c + i], 0.f);
             st_row8_bf16(t.H2, row, c, kHid, v8);
         }
-        ok = tt_issue_wait(t, issuer, [&] { umma_gemm(t.s0, t.H2, 0, kHid, t.w + kW1Bytes + kW2Bytes, 0, kHid, kOutPad, kHid, false); }, a.err);
+        ok = tt_issue_wait(t, issuer, [&] { umma_gemm(t.s0, t.H2, 0, kHid, t.w + kW1Bytes + kW2Bytes, 0, kHid, OUT, kHid, false); }, a.err);
         if (!ok) break;
-        float raw[kOutPad];
-        ld_cols(t.s0, row, kOutPad, raw);
-        for (int i = 0; i < kOutPad; ++i) raw[i] += __ldg(a.f.b3 + i);
+        float raw[OUT];
+        ld_cols(t.s0, row, OUT, raw);
+        for (int i = 0; i < OUT; ++i) raw[i] += __ldg(a.f.b3 + i);
         // ---- loss gradient at the raw outputs ----
-        float dy[kOutPad];
-        if (valid) loss_local += record_grad<D>(a, rec, raw, inv_n, dy);
-        else for (int i = 0; i < kOutPad; ++i) dy[i] = 0.f;
+        float dy[OUT];
+        if (valid) loss_local += record_grad<D, KM>(a, rec, raw, inv_n, dy);
+        else for (int i = 0; i < OUT; ++i) dy[i] = 0.f;
         if (a.loss_only) continue;   // uniform over the tile: no backward pass
-        for (int c = 0; c < kOutPad; c += 8) st_row8_split(t.G, t.Gl, row, c, 128, dy + c);
+        for (int c = 0; c < OUT; c += 8) st_row8_split(t.G, t.Gl, row, c, GC, dy + c);
         {
             float z8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            st_row8_bf16(t.G, row, kOutPad, 128, z8);
-            st_row8_bf16(t.G, row, kOutPad + 8, 128, z8);
-            st_row8_bf16(t.Gl, row, kOutPad, 128, z8);
-            st_row8_bf16(t.Gl, row, kOutPad + 8, 128, z8);
+            for (int c = OUT; c < Z2; c += 8) {
+                st_row8_bf16(t.G, row, c, GC, z8);
+                st_row8_bf16(t.Gl, row, c, GC, z8);
+            }
         }
         // dH2 = dY W3 (W3 image rows = outputs = K here -> MN-major B)
         ok = tt_issue_wait(t, issuer, [&] {
             const uint8_t *W3 = t.w + kW1Bytes + kW2Bytes;
-            umma_gemm(t.s0, t.G, 0, 128, W3, 1, kHid, kHid, kOutPad, false);
-            umma_gemm(t.s0, t.Gl, 0, 128, W3, 1, kHid, kHid, kOutPad, true);
+            umma_gemm(t.s0, t.G, 0, GC, W3, 1, kHid, kHid, OUT, false);
+            umma_gemm(t.s0, t.Gl, 0, GC, W3, 1, kHid, kHid, OUT, true);
         }, a.err);
         if (!ok) break;
         // bias gradient: column sums of the dY tiles (hi + lo, what the MMAs see)
-        if (row < kOutPad) {
+        if (row < OUT) {
             float s = 0.f;
             for (int r = 0; r < 128; ++r)
-                s += __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(t.G + cm_offset(r, row, 128))) +
-                     __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(t.Gl + cm_offset(r, row, 128)));
+                s += __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(t.G + cm_offset(r, row, GC))) +
+                     __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(t.Gl + cm_offset(r, row, GC)));
             db3 += s;
         }
         ld_cols(t.s0, row, kHid, h);
@@ -307,15 +327,16 @@ __global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
             for (int c = 0; c < kHid; c += 8) {
                 float v8[8];
                 for (int i = 0; i < 8; ++i) v8[i] = h2[c + i] > 0.f ? h[c + i] : 0.f;
-                st_row8_split(t.G, t.Gl, row, 64 + c, 128, v8);
+                st_row8_split(t.G, t.Gl, row, Z2 + c, GC, v8);
             }
         }
-        // dW3 (+)= [dY|dZ2]^T H2 (rows 0..47 used); dH1 = dZ2 W2
+        // dW3 (+)= [dY|..]^T H2 over G's first 128 columns (rows 0..OUT-1 used);
+        // dH1 = dZ2 W2
         ok = tt_issue_wait(t, issuer, [&] {
-            umma_gemm(t.acc3, t.G, 1, 128, t.H2, 1, kHid, kHid, 128, have_acc);
-            umma_gemm(t.acc3, t.Gl, 1, 128, t.H2, 1, kHid, kHid, 128, true);
-            umma_gemm(t.s0, t.G + cm_offset(0, 64, 128), 0, 128, t.w + kW1Bytes, 1, kHid, kHid, kHid, false);
-            umma_gemm(t.s0, t.Gl + cm_offset(0, 64, 128), 0, 128, t.w + kW1Bytes, 1, kHid, kHid, kHid, true);
+            umma_gemm(t.acc3, t.G, 1, GC, t.H2, 1, kHid, kHid, 128, have_acc);
+            umma_gemm(t.acc3, t.Gl, 1, GC, t.H2, 1, kHid, kHid, 128, true);
+            umma_gemm(t.s0, t.G + cm_offset(0, Z2, GC), 0, GC, t.w + kW1Bytes, 1, kHid, kHid, kHid, false);
+            umma_gemm(t.s0, t.Gl + cm_offset(0, Z2, GC), 0, GC, t.w + kW1Bytes, 1, kHid, kHid, kHid, true);
         }, a.err);
         if (!ok) break;
         ld_cols(t.s0, row, kHid, h);
@@ -325,17 +346,18 @@ __global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
             for (int c = 0; c < kHid; c += 8) {
                 float v8[8];
                 for (int i = 0; i < 8; ++i) v8[i] = h1[c + i] > 0.f ? h[c + i] : 0.f;
-                st_row8_split(t.G, t.Gl, row, c, 128, v8);
+                st_row8_split(t.G, t.Gl, row, c, GC, v8);
             }
         }
-        // dW2 (+)= [dZ1|dZ2]^T H1 (rows 64..127), dW1 (+)= [dZ1|dZ2]^T X (rows 0..63), dX = dZ1 W1
+        // dW2 (+)= G[:, Z2-64 .. Z2+64)^T H1 (rows 64..127 = dZ2^T H1), dW1 (+)=
+        // G[:, 0..128)^T X (rows 0..63 = dZ1^T X), dX = dZ1 W1
         ok = tt_issue_wait(t, issuer, [&] {
-            umma_gemm(t.acc2, t.G, 1, 128, t.H1, 1, kHid, kHid, 128, have_acc);
-            umma_gemm(t.acc2, t.Gl, 1, 128, t.H1, 1, kHid, kHid, 128, true);
-            umma_gemm(t.acc1, t.G, 1, 128, t.X, 1, kFeat, kFeat, 128, have_acc);
-            umma_gemm(t.acc1, t.Gl, 1, 128, t.X, 1, kFeat, kFeat, 128, true);
-            umma_gemm(t.s0, t.G, 0, 128, t.w, 1, kFeat, kFeat, kHid, false);
-            umma_gemm(t.s0, t.Gl, 0, 128, t.w, 1, kFeat, kFeat, kHid, true);
+            umma_gemm(t.acc2, t.G + cm_offset(0, Z2 - 64, GC), 1, GC, t.H1, 1, kHid, kHid, 128, have_acc);
+            umma_gemm(t.acc2, t.Gl + cm_offset(0, Z2 - 64, GC), 1, GC, t.H1, 1, kHid, kHid, 128, true);
+            umma_gemm(t.acc1, t.G, 1, GC, t.X, 1, kFeat, kFeat, 128, have_acc);
+            umma_gemm(t.acc1, t.Gl, 1, GC, t.X, 1, kFeat, kFeat, 128, true);
+            umma_gemm(t.s0, t.G, 0, GC, t.w, 1, kFeat, kFeat, kHid, false);
+            umma_gemm(t.s0, t.Gl, 0, GC, t.w, 1, kFeat, kFeat, kHid, true);
         }, a.err);
         if (!ok) break;
         have_acc = true;
@@ -364,7 +386,7 @@ __global__ void __launch_bounds__(kTrainBlock, 1) train_kernel(TrainArgs a) {
         float v[kHid];
         ld_cols(t.acc3, row, kHid, v);
         // internal output row -> exchange row (padding and disabled lobes: none)
-        const int er = row < kOutPad ? out_row_to_exchange(row, a.f.dim, a.f.K) : -1;
+        const int er = row < OUT ? out_row_to_exchange(row, a.f.dim, a.f.K, KM) : -1;
         if (er >= 0) for (int i = 0; i < kHid; ++i) atomicAdd(a.g_W3 + (size_t)er * kHid + i, v[i]);
         ld_cols(t.acc2, row, kHid, v);
         if (row >= 64) for (int i = 0; i < kHid; ++i) atomicAdd(a.g_W2 + (size_t)(row - 64) * kHid + i, v[i]);
@@ -453,8 +475,11 @@ __global__ void grid_to_half_kernel(const float *g32, __half2 *g16, int64_t n) {
     if (i < n) g16[i] = __floats2half2_rn(g32[2 * i], g32[2 * i + 1]);
 }
 
-// FP32 MLP master (exchange layout) -> BF16 core-matrix weight image + padded bias
+// FP32 MLP master (exchange layout) -> BF16 core-matrix weight image + padded
+// bias, in the internal output layout of KM lobes
+template <int KM>
 __global__ void weight_image_kernel(const float *mlp, int nout, int dim, int K, uint8_t *img, float *b3pad) {
+    constexpr int OUT = out_pad(KM);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float *W1 = mlp, *W2 = W1 + kHid * kFeat, *W3 = W2 + kHid * kHid, *b3 = W3 + nout * kHid;
     __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(img);
@@ -466,22 +491,27 @@ __global__ void weight_image_kernel(const float *mlp, int nout, int dim, int K, 
         int r = i / kHid, c = i % kHid;
         o[(kW1Bytes + cm_offset(r, c, kHid)) / 2] = __float2bfloat16_rn(W2[i]);
     }
-    if (i < kOutPad * kHid) {
+    if (i < OUT * kHid) {
         int r = i / kHid, c = i % kHid;
-        const int er = out_row_to_exchange(r, dim, K);
+        const int er = out_row_to_exchange(r, dim, K, KM);
         float val = er >= 0 ? W3[er * kHid + c] : 0.f;
         o[(kW1Bytes + kW2Bytes + cm_offset(r, c, kHid)) / 2] = __float2bfloat16_rn(val);
     }
-    if (i < kOutPad) {
-        const int er = out_row_to_exchange(i, dim, K);
-        b3pad[i] = er >= 0 ? b3[er] : (is_off_lambda(i, dim, K) ? kOffLambda : 0.f);
+    if (i < OUT) {
+        const int er = out_row_to_exchange(i, dim, K, KM);
+        b3pad[i] = er >= 0 ? b3[er] : (is_off_lambda(i, dim, K, KM) ? kOffLambda : 0.f);
     }
 }
 
 // BF16 weight image and padded bias from the FP32 MLP masters
 static wost_status refresh_weight_image(wost_field *f, cudaStream_t st) {
-    weight_image_kernel<<<(kHid * kHid + 255) / 256, 256, 0, st>>>(f->mlp32, f->nout, f->desc.dim, f->desc.K,
-                                                                    f->wimg, f->b3pad);
+    constexpr int n8 = kHid * std::max(kHid, out_pad(kMaxK)), n16 = kHid * std::max(kHid, out_pad(kMaxKWide));
+    if (f->km == kMaxK)
+        weight_image_kernel<kMaxK><<<(n8 + 255) / 256, 256, 0, st>>>(f->mlp32, f->nout, f->desc.dim, f->desc.K,
+                                                                     f->wimg, f->b3pad);
+    else
+        weight_image_kernel<kMaxKWide><<<(n16 + 255) / 256, 256, 0, st>>>(f->mlp32, f->nout, f->desc.dim,
+                                                                          f->desc.K, f->wimg, f->b3pad);
     WOST_CUDA(cudaGetLastError());
     return WOST_OK;
 }
@@ -545,8 +575,15 @@ wost_status train_prepare(int dim) {
     static bool attr[4] = {false, false, false, false};
     if (dim != 2 && dim != 3) return WOST_ERR_INVALID_ARG;
     if (!attr[dim]) {
-        if (dim == 2) WOST_CUDA(cudaFuncSetAttribute(train_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem));
-        else WOST_CUDA(cudaFuncSetAttribute(train_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrainSmem));
+        const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        constexpr int s8 = train_smem(kMaxK), s16 = train_smem(kMaxKWide);
+        if (dim == 2) {
+            WOST_CUDA(cudaFuncSetAttribute(train_kernel<2, kMaxK>, at, s8));
+            WOST_CUDA(cudaFuncSetAttribute(train_kernel<2, kMaxKWide>, at, s16));
+        } else {
+            WOST_CUDA(cudaFuncSetAttribute(train_kernel<3, kMaxK>, at, s8));
+            WOST_CUDA(cudaFuncSetAttribute(train_kernel<3, kMaxKWide>, at, s16));
+        }
         attr[dim] = true;
     }
     return WOST_OK;
@@ -585,8 +622,15 @@ wost_status train_grad_launch(wost_field *f, int dim, cudaStream_t st, long long
     // one CTA per SM: each CTA holds all 512 TMEM columns of its SM
     wost_status rc = train_prepare(dim);
     if (rc != WOST_OK) return rc;
-    if (dim == 2) train_kernel<2><<<num_sms(), kTrainBlock, kTrainSmem, st>>>(a);
-    else train_kernel<3><<<num_sms(), kTrainBlock, kTrainSmem, st>>>(a);
+    constexpr int b8 = train_block(kMaxK), b16 = train_block(kMaxKWide);
+    constexpr int s8 = train_smem(kMaxK), s16 = train_smem(kMaxKWide);
+    if (f->km == kMaxK) {
+        if (dim == 2) train_kernel<2, kMaxK><<<num_sms(), b8, s8, st>>>(a);
+        else train_kernel<3, kMaxK><<<num_sms(), b8, s8, st>>>(a);
+    } else {
+        if (dim == 2) train_kernel<2, kMaxKWide><<<num_sms(), b16, s16, st>>>(a);
+        else train_kernel<3, kMaxKWide><<<num_sms(), b16, s16, st>>>(a);
+    }
     if (!loss_only && a.gc.n > 0)
         priv_reduce_kernel<<<(a.gc.start[a.gc.n] + 255) / 256, 256, 0, st>>>(reinterpret_cast<float2 *>(f->grid_g), a.gc);
     WOST_CUDA(cudaGetLastError());

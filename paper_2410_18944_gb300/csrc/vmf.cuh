@@ -67,19 +67,21 @@ __device__ __forceinline__ float half_dist2(const float *mu, const float *nu) {
     return 0.5f * s;
 }
 
-// Normalised mixture parameters of one position (Tab. reg_map).
-template <int D>
+// Normalised mixture parameters of one position (Tab. reg_map), room for
+// KC lobes.
+template <int D, int KC = kMaxKTheta>
 struct Mixture {
-    float mu[kMaxKTheta * D];
-    float kappa[kMaxKTheta];
-    float lam[kMaxKTheta];
-    float lognorm[kMaxKTheta];
+    float mu[KC * D];
+    float kappa[KC];
+    float lam[KC];
+    float lognorm[KC];
     float c;
 };
 
 // raw layout: mu'_i (K x d), kappa'_i (K), lambda'_i (K), c'
-template <int D, int K>
-__device__ __forceinline__ void theta_map(const float *raw, Mixture<D> &m) {
+template <int D, int K, int KC>
+__device__ __forceinline__ void theta_map(const float *raw, Mixture<D, KC> &m) {
+    static_assert(K <= KC, "mixture capacity");
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         float s = 0.f;
@@ -104,8 +106,8 @@ __device__ __forceinline__ void theta_map(const float *raw, Mixture<D> &m) {
     m.c = 1.f / (1.f + __expf(-raw[K * (D + 2)]));
 }
 
-template <int D, int K>
-__device__ __forceinline__ float mixture_pdf(const Mixture<D> &m, const float *nu) {
+template <int D, int K, int KC>
+__device__ __forceinline__ float mixture_pdf(const Mixture<D, KC> &m, const float *nu) {
     float p = 0.f;
 #pragma unroll
     for (int i = 0; i < K; ++i) p += m.lam[i] * __expf(m.lognorm[i] - m.kappa[i] * half_dist2<D>(m.mu + i * D, nu));
@@ -165,8 +167,8 @@ __device__ __forceinline__ void vmf3_sample(float k, const float *mu, float xi, 
 // mixture (lobe by the lambda-CDF, then a vMF sample), else the uniform
 // sphere; the caller reflects below the tangent plane (Sec. 4.3).
 // Returns true if the mixture was sampled.
-template <int D, int K>
-__device__ __forceinline__ bool sample_direction(const Mixture<D> &m, float c, uint32_t pid, uint32_t wid,
+template <int D, int K, int KC>
+__device__ __forceinline__ bool sample_direction(const Mixture<D, KC> &m, float c, uint32_t pid, uint32_t wid,
                                                  uint32_t step, uint32_t k0, uint32_t k1, float *nu) {
     U4 u = philox(pid, wid, step, P_MIS, k0, k1);
     if (u01(u.x) < c) {

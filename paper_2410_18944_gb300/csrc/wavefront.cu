@@ -268,6 +268,10 @@ int occupancy_grid(K kernel, int block, size_t smem) {
 // set by the caller) through the wavefront; returns the iterations taken.
 wost_status wavefront_run(wost_scene *sc, wost_field *f, const WalkArgs &a, const WsOpts &o, const RecDest &rd,
                           int max_slots, cudaStream_t st, int64_t *iters_out) {
+    if (f->km != kMaxK) {
+        set_error("wost_solve: the wavefront kernel serves fields of at most 8 lobes");
+        return WOST_ERR_UNSUPPORTED;
+    }
     const int D = sc->dim;
     const unsigned long long items = a.total;
     const int nslots = (int)std::min<unsigned long long>(items, (unsigned long long)std::max(max_slots, 1));

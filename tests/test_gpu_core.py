@@ -115,11 +115,12 @@ def _rand_mixture(rng, n, dim, K=8, kmax=200.0):
     return mu.astype(np.float32), kap.astype(np.float32), lam.astype(np.float32)
 
 
+@pytest.mark.parametrize("K", [8, 16])
 @pytest.mark.parametrize("dim", [2, 3])
-def test_mixture_pdf_parity(api, dim):
-    rng = np.random.default_rng(10 + dim)
+def test_mixture_pdf_parity(api, dim, K):
+    rng = np.random.default_rng(10 + dim + 100 * (K // 16))
     n = 4000
-    mu, kap, lam = _rand_mixture(rng, n, dim)
+    mu, kap, lam = _rand_mixture(rng, n, dim, K=K)
     nu = rng.normal(size=(n, dim))
     nu /= np.linalg.norm(nu, axis=1, keepdims=True)
     # half the directions close to a lobe mean (the density's bulk)
@@ -139,11 +140,12 @@ def test_mixture_pdf_parity(api, dim):
     assert np.all(rel[big] < 1e-5), rel[big].max()
 
 
+@pytest.mark.parametrize("K", [8, 16])
 @pytest.mark.parametrize("dim", [2, 3])
-def test_mixture_sample_parity(api, dim):
-    rng = np.random.default_rng(20 + dim)
+def test_mixture_sample_parity(api, dim, K):
+    rng = np.random.default_rng(20 + dim + 100 * (K // 16))
     n = 4000
-    mu, kap, lam = _rand_mixture(rng, n, dim, kmax=500.0)
+    mu, kap, lam = _rand_mixture(rng, n, dim, K=K, kmax=500.0)
     ctr = np.stack([np.arange(n), np.full(n, 3), np.full(n, 5)], 1).astype(np.uint32)
     seed = 0x1234567890
     gnu, gpdf = api.mixture_sample(dim, mu, kap, lam, ctr, seed)

@@ -562,15 +562,17 @@ def test_dense_grid_online_training_is_unbiased(api):
 
 
 # ---------------------------------------------------------------------------
-# lobe count (Sec. 6.3 ablation): K = 4 mixtures through the same kernels
+# lobe count (Sec. 6.3 ablation): K = 4 mixtures through the 8-lobe kernels,
+# K = 16 through their 16-lobe variants
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("K", [4, 16])
 @pytest.mark.parametrize("dim", [2, 3])
-def test_four_lobe_field_decode_gradient_and_records(api, dim):
+def test_lobe_count_field_decode_gradient_and_records(api, dim, K):
     sc = _scene_with_source(dim)
     lo, hi = sc.padded_bbox()
-    F = api.Field(dim, lo, hi, K=4)
-    assert F.nout == (dim + 2) * 4 + 1
-    fp = wi.random_field_params(dim, 9, lo, hi, log2T=F.desc.log2_table, K=4, w_scale=0.5)
+    F = api.Field(dim, lo, hi, K=K)
+    assert F.nout == (dim + 2) * K + 1
+    fp = wi.random_field_params(dim, 9, lo, hi, log2T=F.desc.log2_table, K=K, w_scale=0.5)
     fp["grid"] = wi.round_to_fp16(np.abs(fp["grid"]) + 0.05)
     fp["W1"], fp["W2"] = np.abs(fp["W1"]), np.abs(fp["W2"])
     for k in ("W1", "W2", "W3"):
@@ -596,7 +598,68 @@ def test_four_lobe_field_decode_gradient_and_records(api, dim):
         cos = gv @ ov / (np.linalg.norm(gv) * np.linalg.norm(ov) + 1e-300)
         rel = np.linalg.norm(gv - ov) / (np.linalg.norm(ov) + 1e-300)
         assert cos > 0.99995 and rel < 1e-2, (name, cos, rel)
-    # recorded walks of a 4-lobe constant mixture, record by record
-    full, first, nrec, n = _compare_records(api, sc, dim, 1, 96, 52 + dim, 53 + dim, K=4)
-    print(f"four lobes dim={dim}: {full}/{n} walks identical ({nrec} records)")
+    # recorded walks of a K-lobe constant mixture, record by record
+    full, first, nrec, n = _compare_records(api, sc, dim, 1, 96, 52 + dim, 53 + dim, K=K)
+    print(f"{K} lobes dim={dim}: {full}/{n} walks identical ({nrec} records)")
     assert first == n and full >= 0.9 * n
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_sixteen_lobe_guided_solve_statistical_bar(api, dim):
+    # a frozen 16-lobe constant mixture: launches without training records,
+    # which 8-lobe fields send to the wavefront, run the 16-lobe
+    # warp-specialised kernel; the statistical bar against the oracle on the
+    # same streams as for 8 lobes
+    sc = _scene_with_source(dim) if dim == 2 else wi.slab_box(2)
+    S, O = api.Scene(sc), oracle.Scene(sc)
+    F, OF = _field_pair_constant(api, dim, sc, seed=64 + dim, K=16, kappa_range=(-2.0, 1.0), c_raw=-0.5)
+    npts, nw = (320, 128) if dim == 2 else (240, 96)
+    pts = _interior(sc, npts, 74 + dim, margin=0.02)
+    eps, maxsteps, seed = 1e-3, 512, 125
+    m, v, st = api.solve(S, pts, nw, eps=eps, maxsteps=maxsteps, seed=seed, guided=True, field=F)
+    r = oracle.solve(O, oracle.make_params(eps=eps, maxsteps=maxsteps, seed=seed, guided=1), pts, 0, nw, field=OF)
+    om, ov = oracle.mean_var(r["sum"], r["sum2"], nw)
+    z = (m - om) / np.sqrt(v + ov)
+    exact = wi.eval_fn(sc.exact, pts)
+    rel = lambda u: float(np.mean((u - exact) ** 2 / (exact ** 2 + 1e-2)))   # noqa: E731
+    rg, ro = rel(m), rel(om)
+    print(f"16 lobes, statistical bar dim={dim}: max |z| {np.abs(z).max():.2f}, relMSE ratio {rg / ro:.4f}")
+    assert np.all(np.abs(z) < 4.0), np.abs(z).max()
+    assert abs(rg / ro - 1) < 0.02
+    assert np.all(np.abs(m - exact) < 4 * np.sqrt(v) + 1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_sixteen_lobe_online_training_is_unbiased(api, dim):
+    # online training of a 16-lobe field (one 128-record tile per SM in the
+    # training kernel): estimates stay unbiased against the closed form and
+    # the trained parameters finite
+    sc = wi.half_disk(48, 12) if dim == 2 else wi.slab_box(2)
+    S = api.Scene(sc)
+    F = api.Field(dim, *sc.padded_bbox(), K=16)
+    pts = _interior(sc, 128 if dim == 2 else 96, 43 + dim, margin=0.05)
+    m, v, st = api.solve(S, pts, 256, eps=1e-3, maxsteps=512, seed=15 + dim, guided=True, field=F, train=1,
+                         train_until_wpp=16)
+    assert st["train_steps"] == 16 and st["records"] > 0
+    z = (m - wi.eval_fn(sc.exact, pts)) / np.sqrt(v)
+    print(f"16 lobes, online training dim={dim}: {np.mean(np.abs(z) < 4.0):.4f} of points within 4 SE")
+    assert np.all(np.isfinite(m)) and np.mean(np.abs(z) < 4.0) > 0.98
+    p = F.get_params()
+    assert all(np.all(np.isfinite(p[k])) for k in ("grid", "W1", "W2", "W3", "b3"))
+
+
+def test_sixteen_lobe_field_rejected_where_unsupported(api):
+    from paper_2410_18944_gb300 import _lib
+    sc = wi.half_disk(16, 4)
+    S = api.Scene(sc)
+    F = api.Field(2, *sc.padded_bbox(), K=16)
+    pts = np.array([[0.0, 0.4], [0.2, 0.3]])
+    with pytest.raises(_lib.WostError, match="wavefront"):
+        api.solve(S, pts, 4, guided=True, field=F, guided_kernel=2)
+    with pytest.raises(_lib.WostError, match="walker count"):
+        api.solve(S, pts, 4, guided=True, field=F, walker_warps=28)
+    pd = torch.tensor(pts, dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.WostError, match="at most 8 lobes"):
+        api.Batch([dict(scene=S, points=pd, nwalks=2, field=F)], guided=True)
+    with pytest.raises(_lib.WostError):
+        api.Field(2, K=17)

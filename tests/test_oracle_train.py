@@ -27,9 +27,10 @@ def _setup(dim, seed=0, H=16, K=4, grid_type=0):
     return fp, recs
 
 
-@pytest.mark.parametrize("dim,c_mode,grid_type", [(2, 0, 0), (3, 0, 0), (2, 1, 0), (2, 0, 1), (3, 0, 1)])
-def test_gradient_matches_central_differences(dim, c_mode, grid_type):
-    fp, recs = _setup(dim, grid_type=grid_type)
+@pytest.mark.parametrize("dim,c_mode,grid_type,K", [(2, 0, 0, 4), (3, 0, 0, 4), (2, 1, 0, 4), (2, 0, 1, 4), (3, 0, 1, 4),
+                                                    (2, 0, 0, 16), (3, 0, 0, 16)])
+def test_gradient_matches_central_differences(dim, c_mode, grid_type, K):
+    fp, recs = _setup(dim, grid_type=grid_type, K=K)
     f = oracle.Field(fp)
     loss0, grads, pg0 = f.train_loss(recs, c_mode=c_mode, c_fixed=0.7)
     rng = np.random.default_rng(1)

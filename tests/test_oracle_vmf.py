@@ -61,10 +61,10 @@ def test_vmf3_normalised(kappa):
     assert s == pytest.approx(1.0, abs=1e-10)
 
 
+@pytest.mark.parametrize("K", [8, 16])
 @pytest.mark.parametrize("kappa", [0.5, 5.0, 60.0])
-def test_mixture_and_reflected_density_normalised(kappa):
+def test_mixture_and_reflected_density_normalised(kappa, K):
     rng = np.random.default_rng(0)
-    K = 8
     # 2D: the reflected guided density V(nu) + V(nu^-) on the half circle
     # nu . n > 0 integrates to one (Sec. 4.3)
     mu = rng.normal(size=(K, 2))
