@@ -85,7 +85,7 @@ WORKLOADS = {
     "ablations": dict(workload="ablations of Sec. 6.2-6.3 and Tab. mis: on the 81,920-triangle icosphere (64 "
                                "walks/point, training batches of 8 walks/point in minibatches) the MIS modes "
                                "(uniform only c = 0, fixed c = 0.5, guiding only c = 1, learned c), sample "
-                               "reflection off, K = 4 against 8 lobes, and training batches of 1, 4 and 16 "
+                               "reflection off, K = 4 and 16 against 8 lobes, and training batches of 1, 4 and 16 "
                                "walks/point; "
                                "on "
                                "the 4096-segment star (512 walks/point) the training budget train_until_wpp in "
@@ -665,6 +665,7 @@ def ablation_line(ctx, args):
         ("uniform only, c = 0", {}, dict(c_mode=1, c_fixed=0.0)),
         ("no sample reflection", {}, dict(reflect=0)),
         ("K = 4 lobes", dict(K=4), {}),
+        ("K = 16 lobes", dict(K=16), {}),
         ("training batch of 1 walk/point", {}, dict(batch_wpp=1)),
         ("training batch of 4 walks/point", {}, dict(batch_wpp=4)),
         ("training batch of 16 walks/point", {}, dict(batch_wpp=16)),
