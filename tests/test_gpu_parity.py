@@ -397,6 +397,36 @@ def test_guided_solve_statistical_bar(api, dim):
     assert np.all(np.abs(m - exact) < 4 * np.sqrt(v) + 1e-12)
 
 
+def test_small_laplace_workload_vs_oracle_and_closed_form(api):
+    # the small 2D Laplace workload in full: the 64-gon with g = e^x cos y,
+    # the 32 x 32 grid of [-1, 1]^2 clipped to the interior, 64 plain walks
+    # per point, eps 1e-3, at most 128 steps; the GPU and the oracle on the
+    # same random streams, and both against the closed form u = g
+    sc, pts = wi.config_small_laplace()
+    S, O = api.Scene(sc), oracle.Scene(sc)
+    n, eps, maxsteps, seed = 64, 1e-3, 128, 2024
+    m, v, st = api.solve(S, pts, n, eps=eps, maxsteps=maxsteps, seed=seed)
+    r = oracle.solve(O, oracle.make_params(eps=eps, maxsteps=maxsteps, seed=seed), pts, 0, n)
+    om, ov = oracle.mean_var(r["sum"], r["sum2"], n)
+    assert len(pts) > 700 and st["walks"] == n * len(pts) and st["truncated"] == 0
+    z = (m - om) / np.sqrt(v + ov)
+    exact = wi.eval_fn(sc.exact, pts)
+    rel = lambda u: float(np.mean((u - exact) ** 2 / (exact ** 2 + 1e-2)))   # noqa: E731
+    rg, ro = rel(m), rel(om)
+    print(f"small Laplace workload: {len(pts)} points, max |z| vs oracle {np.abs(z).max():.3f}, "
+          f"relMSE GPU {rg:.4e} oracle {ro:.4e}, walk-steps {st['walk_steps']} vs {r['steps']}")
+    assert np.all(np.abs(z) < 4.0) and np.median(np.abs(z)) < 0.3
+    assert abs(rg / ro - 1) < 0.02
+    assert abs(st["walk_steps"] - r["steps"]) / r["steps"] < 0.02
+    # each unbiased: the mean error over the points within 4 of its standard
+    # errors (per point, 64 walks under-sample the rare walks that reach the
+    # far side of the disk, where g = e^x cos y is largest, so per-point
+    # z-scores against the closed form are not a fair test at this size)
+    for u, var in ((m, v), (om, ov)):
+        e, se = float(np.mean(u - exact)), float(np.sqrt(np.sum(var)) / len(pts))
+        assert abs(e) < 4 * se + 1e-3, (e, se)
+
+
 # ---------------------------------------------------------------------------
 # nonzero Neumann flux (Sec. 3.2, Eq. wost_estm, the -<N> term)
 # ---------------------------------------------------------------------------
