@@ -229,7 +229,10 @@ wost_status wost_scene_bbox(const wost_scene *scene, double lo[3], double hi[3])
    exec->train the field is trained after every batch of exec->batch_wpp
    walks per point (one by default, Sec. 5.2) until train_until_wpp walks per
    point.  Batches run in order,
-   so the estimate is deterministic up to floating-point atomics. */
+   so the estimate is deterministic up to floating-point atomics.  One walk
+   per point gives variance 0 (no sample variance from one sample).  With
+   npoints == 0 the call does nothing and returns WOST_OK; points and the
+   outputs may then be NULL. */
 wost_status wost_solve(wost_scene *scene, wost_field *field, const double *points,
                        int64_t npoints, int32_t nwalks, double eps, int32_t maxsteps,
                        int32_t guided, double *out_mean, double *out_var, wost_stats *stats,

@@ -214,7 +214,7 @@ wost_status device_check(cudaStream_t st) { return check_err_flag(st); }
 extern "C" wost_status wost_solve(wost_scene *s, wost_field *field, const double *points, int64_t npoints,
                                   int32_t nwalks, double eps, int32_t maxsteps, int32_t guided,
                                   double *out_mean, double *out_var, wost_stats *stats, const wost_exec *exec) {
-    if (!s || !out_mean || npoints < 0 || nwalks <= 0 || !(eps > 0) || maxsteps < 0) {
+    if (!s || (npoints > 0 && !out_mean) || npoints < 0 || nwalks <= 0 || !(eps > 0) || maxsteps < 0) {
         set_error("wost_solve: invalid argument");
         return WOST_ERR_INVALID_ARG;
     }
