@@ -8,11 +8,14 @@ sphere displaced by 0.15 Perlin noise minus three smoothly rimmed tunnels,
 data g = 1/|x - c|; queries on the 1024 x 1024 slice z = 0 masked inside
 (510,479 points) at 128 walks per point; guided sampling from the 3D
 hash-grid + MLP vMF mixture field with learned MIS selection, trained online
-after every batch of one walk per point in minibatches of 2^18 records
-(fused tcgen05 backward + Adam).
+after every batch of two walks per point in minibatches of 2^18 records
+(fused tcgen05 backward + Adam).  The paper trains after batches of one walk
+per point of a 1024 x 1024 grid, about 2^20 walks; the slice keeps half of
+its points inside the solid, so two walks per point make a batch of that
+size (1.02 M walks).
 
-One "step" is one training round of the full slice: one walk per point
-(510,479 walks, every hot-path stage) followed by that batch's Adam steps.
+One "step" is one training round of the full slice: two walks per point
+(1,020,958 walks, every hot-path stage) followed by that batch's Adam steps.
 W rounds warm up, K rounds are timed (CUDA events on the launching stream),
 and the remaining rounds of the 128-walk solve run untimed to complete the
 estimate for the equal-time relMSE.  The BVHs (about 300 MB) and the
@@ -59,11 +62,12 @@ WORKLOADS = {
     "genus3": dict(workload="3D mixed Dirichlet/Neumann Laplace guided WoSt with learned MIS selection: genus-3 "
                             "solid (sphere displaced by 0.15 Perlin noise minus three smoothly rimmed tunnels, "
                             "993,640 triangles by surface nets), 30% Neumann cap, g = 1/|x - c|, 1024x1024 slice "
-                            "z = 0 masked inside, 128 walks/point, online training after every batch of one walk per point in minibatches "
+                            "z = 0 masked inside, 128 walks/point, online training after every batch of two walks per point "
+                            "(1.02 M walks, the paper's 2^20-walk batch) in minibatches "
                             "of 2^18 records, 16-level 2^19-entry FP16 hash grid + 32-64-64-41 BF16 MLP, K = 8",
                    dim=3, grid=1024, spp=128, eps=1e-3, maxsteps=128, train_samples=1 << 18, subset=4096,
-                   ref_factor=64, batch_wpp=1,
-                   step="one training batch: one walk per point of the slice (510k walks) + its Adam steps",
+                   ref_factor=64, batch_wpp=2,
+                   step="one training batch: two walks per point of the slice (1.02M walks) + its Adam steps",
                    l2="inputs larger than L2 (about 300 MB of BVH, 510k-walk batches); no flush"),
     "sphere3d": dict(workload="3D mixed Dirichlet/Neumann Poisson guided WoSt: icosphere 81,920 triangles displaced "
                               "by 0.15 Perlin noise, 30% Neumann cap, f = 4 Gaussians (sigma 0.1), g = 1/|x - c|, "
@@ -439,6 +443,12 @@ def guided_rounds_line(ctx, key, args, rank=0, world=1, full=True):
             "dtype": DTYPE, "data": "synthetic",
             "config": dict(W, points=npts, parallelism=f"replicas x{world}"), "clocks": clk.summary(),
             "gpu_launches": int(round(sum(s["kernel_launches"] for s in stats) / len(stats)))}
+    # every walk ends in exactly one terminal step (the closest-point query
+    # that finds it in the eps-shell, or the step cap): the rate of the
+    # steps that move a walk
+    walks_here = sum(s["walks"] for s in stats)
+    steps_here = sum(s["walk_steps"] for s in stats)
+    line["non_terminal_walk_steps_per_s"] = value * (steps_here - walks_here) / max(steps_here, 1)
     if not full or rank != 0:
         return line, None
     # the rest of the solve (untimed): every round of the spp-walk estimate
@@ -768,9 +778,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-relmse", action="store_true", help="skip the equal-time relMSE measurement")
     ap.add_argument("--no-extras", action="store_true", help="the main line only")
+    ap.add_argument("--batch-wpp", type=int, default=0,
+                    help="walks per point in one training batch of the main workload (default: the workload's)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.batch_wpp > 0:
+        W = WORKLOADS[args.workload]
+        W["batch_wpp"] = args.batch_wpp
+        W["workload"] += f"; training batches of {args.batch_wpp} walks per point"
     if args.once:
         return run_once(args)
     if args.impl == "reference":

@@ -242,6 +242,76 @@ wost_status launch_guided(int dim, const GuidedArgs &g, int grid, cudaStream_t s
     return WOST_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Longest walks first.  A launch of the warp-specialised kernel lasts until
+// its last walk ends, and a walk of a hundred steps or more that starts late
+// keeps the launch running while most walker lanes have nothing left to do.
+// The walks of one point have correlated lengths (points near the Neumann
+// boundary walk long), so after each launch the points are sorted by the
+// walk-steps their walks took in it, longest first (a counting sort on the
+// device, no host round trip), and the next launch hands out each walk
+// index's points in that order.  A walk draws from the random streams of its
+// (point, walk) pair whenever it runs: the order changes no walk, only
+// which walker lane runs it and when.  The order is kept with the scene
+// from call to call (a solve run batch by batch, one call per training
+// batch, keeps it); a call on another number of points starts afresh, and a
+// call on other points of the same number gets a valid if unhelpful order.
+// ---------------------------------------------------------------------------
+#ifndef WOST_LONGEST_FIRST
+#define WOST_LONGEST_FIRST 1
+#endif
+constexpr int kOrderBins = 1024;   // walk-step counts at or above kOrderBins - 1 share the top bin
+
+__device__ __forceinline__ int order_bin(unsigned len) {
+    return kOrderBins - 1 - (int)min(len, (unsigned)(kOrderBins - 1));   // longest first
+}
+
+__global__ void order_hist_kernel(const unsigned *plen, int64_t n, unsigned *hist) {
+    __shared__ unsigned h[kOrderBins];
+    for (int i = threadIdx.x; i < kOrderBins; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[order_bin(plen[p])], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kOrderBins; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// exclusive prefix sum of the kOrderBins counts, in place (one block of
+// kOrderBins threads)
+__global__ void order_scan_kernel(unsigned *hist) {
+    __shared__ unsigned buf[2][kOrderBins];
+    const int t = threadIdx.x;
+    int in = 0;
+    buf[0][t] = t > 0 ? hist[t - 1] : 0u;
+    __syncthreads();
+    for (int off = 1; off < kOrderBins; off <<= 1) {
+        buf[1 - in][t] = buf[in][t] + (t >= off ? buf[in][t - off] : 0u);
+        in = 1 - in;
+        __syncthreads();
+    }
+    hist[t] = buf[in][t];
+}
+
+__global__ void order_scatter_kernel(const unsigned *plen, int64_t n, unsigned *offset, uint32_t *order) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    order[atomicAdd(&offset[order_bin(plen[p])], 1u)] = (uint32_t)p;
+}
+
+// the next launch's order from this launch's walk lengths (stream-ordered)
+static wost_status order_by_length(const unsigned *plen, int64_t n, unsigned *hist, uint32_t *order,
+                                   cudaStream_t st, int64_t &launches) {
+    WOST_CUDA(cudaMemsetAsync(hist, 0, kOrderBins * sizeof(unsigned), st));
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 4);
+    order_hist_kernel<<<blocks, 256, 0, st>>>(plen, n, hist);
+    order_scan_kernel<<<1, kOrderBins, 0, st>>>(hist);
+    order_scatter_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(plen, n, hist, order);
+    WOST_CUDA(cudaGetLastError());
+    launches += 3;
+    return WOST_OK;
+}
+
 wost_status ensure_records(wost_field *f, int64_t cap, size_t scratch_bytes);
 wost_status wavefront_run(wost_scene *sc, wost_field *f, const WalkArgs &a, const WsOpts &o, const RecDest &rd,
                           int max_slots, cudaStream_t st, int64_t *iters_out);
@@ -367,6 +437,20 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
         }
         g.o.scratch = f->scratch;
         const int ws_walks = ws_then_wavefront ? rounds : nwalks;
+        // walk lengths per point and the launch order (longest walks first)
+        unsigned *plen = nullptr, *hist = nullptr;
+        uint32_t *order = nullptr;
+        const bool longest_first = WOST_LONGEST_FIRST && a.npoints > 1;
+        if (longest_first) {
+            const size_t n = (size_t)a.npoints;
+            const size_t had = s->ws_order.bytes;
+            wost_status rc = s->ws_order.ensure((2 * n + kOrderBins) * sizeof(unsigned));
+            if (rc != WOST_OK) return rc;
+            if (s->ws_order.bytes != had) s->order_n = 0;   // a new buffer holds no order
+            plen = s->ws_order.as<unsigned>();
+            order = reinterpret_cast<uint32_t *>(plen + n);
+            hist = plen + 2 * n;
+        }
         // one launch per training batch (its scratch rows belong to walker
         // lanes, so a launch may hold several walks per point), one launch
         // per walk index after training
@@ -375,15 +459,24 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
             g.w = a;
             g.w.walk_begin = walk_begin + b;
             g.w.total = (unsigned long long)a.npoints * (unsigned long long)nb;
+            g.w.order = longest_first && s->order_n == a.npoints ? order : nullptr;   // else point order
+            g.w.plen = longest_first ? plen : nullptr;
             g.o.record = b < rounds;
             WOST_CUDA(cudaMemsetAsync(a.work_ctr, 0, sizeof(unsigned long long), st));
             if (g.o.record) WOST_CUDA(cudaMemsetAsync(f->rec_ctr, 0, 2 * sizeof(unsigned long long), st));
+            if (g.w.plen) WOST_CUDA(cudaMemsetAsync(plen, 0, (size_t)a.npoints * sizeof(unsigned), st));
             tm.mark(tm.walk, st);
             wost_status rc = launch_guided(s->dim, g, grid, st, walkers, f->km);
             tm.mark(tm.walk, st);
             tm.launches++;
             tm.walk_launches++;
             if (rc != WOST_OK) return rc;
+            // (the order kernels run after the launch and before the
+            // training step, which does not read them)
+            if (g.w.plen) {
+                if ((rc = order_by_length(plen, a.npoints, hist, order, st, tm.launches)) != WOST_OK) return rc;
+                s->order_n = a.npoints;
+            }
             if (g.o.record && (rc = train_after()) != WOST_OK) return rc;
         }
         if (ws_then_wavefront) {

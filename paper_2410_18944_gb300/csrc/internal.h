@@ -46,6 +46,8 @@ struct wost_scene {
     // per-solve workspace (grown on demand)
     wost::DevBuf ws_points, ws_status, ws_sum, ws_sum2, ws_ctr, ws_out;
     wost::DevBuf ws_wf;                        // guided wavefront slots
+    wost::DevBuf ws_order;                     // walk lengths and launch order of the guided launches
+    int64_t order_n = 0;                       // point count the order in ws_order was made for (0: none)
     unsigned long long *pinned = nullptr;      // host-pinned words for wavefront progress
     ~wost_scene();
 };

@@ -52,13 +52,20 @@ struct SoloSrc {
     __device__ __forceinline__ unsigned long long *work_ctr() const { return a.work_ctr; }
     __device__ __forceinline__ unsigned long long total() const { return a.total; }
     __device__ __forceinline__ bool start(Walk<D> &w, unsigned long long item) const {
+        if (a.order) {   // the same walk index, another point
+            const unsigned long long p = item % (unsigned long long)a.npoints;
+            item = item - p + a.order[p];
+        }
         start_walk<D>(w, a, item);
         return a.status[w.pid] == 0;
     }
     __device__ __forceinline__ StepEnv env(const Walk<D> &) const {
         return StepEnv{*sc, a.eps, a.eps64, a.maxsteps, a.key0, a.key1, a.err, a.rr_depth, a.rr_q};
     }
-    __device__ __forceinline__ void finish(const Walk<D> &w) const { finish_walk(a, w.pid, w.acc); }
+    __device__ __forceinline__ void finish(const Walk<D> &w) const {
+        finish_walk(a, w.pid, w.acc);
+        if (a.plen) atomicAdd(a.plen + w.pid, (unsigned)w.k + 1u);
+    }
     __device__ __forceinline__ const DevField &field(const Walk<D> &) const { return *f; }
     __device__ __forceinline__ RecDest rec(const Walk<D> &) const { return rd; }
     __device__ __forceinline__ int job(const Walk<D> &) const { return 0; }

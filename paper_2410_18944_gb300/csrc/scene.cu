@@ -336,6 +336,7 @@ wost_scene::~wost_scene() {
     for (void *p : allocs) cudaFree(p);
     ws_points.release(); ws_status.release(); ws_sum.release(); ws_sum2.release(); ws_ctr.release(); ws_out.release();
     ws_wf.release();
+    ws_order.release();
     if (pinned) cudaFreeHost(pinned);
 }
 

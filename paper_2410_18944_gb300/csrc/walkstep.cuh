@@ -37,6 +37,12 @@ struct WalkArgs {
     int *err;
     int rr_depth;              // Russian roulette from this step on (0 = off)
     float rr_q;                // survival probability of a roulette step
+    // single-scene guided launches only (nullptr elsewhere): the order in
+    // which a launch hands out the points of each walk index (a
+    // permutation of [0, npoints)), and per point the walk-steps its walks
+    // take in this launch
+    const uint32_t *order;
+    unsigned *plen;
 };
 
 // what one step needs besides the walk state: the walk's scene and the
