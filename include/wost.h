@@ -229,7 +229,11 @@ wost_status wost_scene_bbox(const wost_scene *scene, double lo[3], double hi[3])
    exec->train the field is trained after every batch of exec->batch_wpp
    walks per point (one by default, Sec. 5.2) until train_until_wpp walks per
    point.  Batches run in order,
-   so the estimate is deterministic up to floating-point atomics.  One walk
+   so the estimate is deterministic up to floating-point atomics.  Guided
+   launches of the warp-specialised kernel hand out their points longest
+   walks first, by the walk lengths of the scene's previous such launch on
+   as many points; a walk's random numbers depend only on its (point, walk)
+   pair, so this order changes no estimate.  One walk
    per point gives variance 0 (no sample variance from one sample).  With
    npoints == 0 the call does nothing and returns WOST_OK; points and the
    outputs may then be NULL. */

@@ -440,7 +440,7 @@ wost_status guided_solve(wost_scene *s, wost_field *f, WalkArgs &a, int nwalks, 
         // walk lengths per point and the launch order (longest walks first)
         unsigned *plen = nullptr, *hist = nullptr;
         uint32_t *order = nullptr;
-        const bool longest_first = WOST_LONGEST_FIRST && a.npoints > 1;
+        const bool longest_first = WOST_LONGEST_FIRST && a.npoints > 1 && a.npoints < (int64_t)UINT32_MAX;
         if (longest_first) {
             const size_t n = (size_t)a.npoints;
             const size_t had = s->ws_order.bytes;
