@@ -192,8 +192,8 @@ static int stage_budget_bytes() {
 }
 
 wost_status guided_occupancy(int dim, int *per_sm) {
-    static bool set[4] = {false, false, false, false};
-    if (!set[dim]) {
+    *per_sm = 1;
+    return once_per_device(100 + dim, [&]() -> wost_status {
         const int bytes = kWsSmem + stage_budget_bytes();
         const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
         // (the 16-lobe kernel stages less of the scene: the same total)
@@ -208,10 +208,8 @@ wost_status guided_occupancy(int dim, int *per_sm) {
             WOST_CUDA(cudaFuncSetAttribute(guided_walk_kernel<3, kWsWalkerWarps, kMaxKWide>, at,
                                            std::max(bytes, ws_smem_bytes(false, kMaxKWide))));
         }
-        set[dim] = true;
-    }
-    *per_sm = 1;
-    return WOST_OK;
+        return WOST_OK;
+    });
 }
 
 // regions of the scene to stage, and their size in float4 (km: lobe

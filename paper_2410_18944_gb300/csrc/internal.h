@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -29,6 +30,11 @@ struct DevBuf {
 };
 
 struct FieldDev;  // defined in field.cuh
+
+// Kernel attributes belong to a device: set-up that must run once per device
+// (and per key) runs under a lock the first time it is asked for while that
+// device is current; a failed set-up runs again on the next call.
+wost_status once_per_device(int key, const std::function<wost_status()> &f);
 
 }  // namespace wost
 

@@ -572,9 +572,8 @@ int train_step_launches(const wost_field *f) { return 4 + (grad_copies(f).n > 0 
 // one-time kernel attributes (also called before a stream capture, where
 // the launches follow without further set-up)
 wost_status train_prepare(int dim) {
-    static bool attr[4] = {false, false, false, false};
     if (dim != 2 && dim != 3) return WOST_ERR_INVALID_ARG;
-    if (!attr[dim]) {
+    return once_per_device(200 + dim, [&]() -> wost_status {
         const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
         constexpr int s8 = train_smem(kMaxK), s16 = train_smem(kMaxKWide);
         if (dim == 2) {
@@ -584,9 +583,8 @@ wost_status train_prepare(int dim) {
             WOST_CUDA(cudaFuncSetAttribute(train_kernel<3, kMaxK>, at, s8));
             WOST_CUDA(cudaFuncSetAttribute(train_kernel<3, kMaxKWide>, at, s16));
         }
-        attr[dim] = true;
-    }
-    return WOST_OK;
+        return WOST_OK;
+    });
 }
 
 // gradient of the mean loss over the record buffer into f->grid_g / f->mlp_g

@@ -11,6 +11,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <vector>
 
 #include "field.cuh"
@@ -31,6 +33,18 @@ double walk_alg_bytes(int D, bool guided, const unsigned long long *hs, int64_t 
         b += (double)records * (48.0 + 48.0 + 48.0);     // record write, suffix read, final write
     }
     return b;
+}
+
+wost_status once_per_device(int key, const std::function<wost_status()> &f) {
+    static std::mutex m;
+    static std::set<std::pair<int, int>> done;
+    int dev = 0;
+    WOST_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(m);
+    if (done.count({dev, key})) return WOST_OK;
+    const wost_status rc = f();
+    if (rc == WOST_OK) done.insert({dev, key});
+    return rc;
 }
 
 int num_sms() {

@@ -309,15 +309,21 @@ wost_status wavefront_run(wost_scene *sc, wost_field *f, const WalkArgs &a, cons
         WOST_CUDA(cudaMemsetAsync(S.ended, 0, n * sizeof(int2), st));
     }
 
+    // decode grid: the attribute is set, and the occupancy taken, once per
+    // device (the device model, and so the grid, is the same on all of them)
     static int grid_dec[4] = {0, 0, 0, 0};
-    if (!grid_dec[D]) {
-        if (D == 2) {
-            WOST_CUDA(cudaFuncSetAttribute(wf_decode_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCtaTilesSmem));
-            grid_dec[D] = occupancy_grid(wf_decode_kernel<2>, 256, kCtaTilesSmem);
-        } else {
-            WOST_CUDA(cudaFuncSetAttribute(wf_decode_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCtaTilesSmem));
-            grid_dec[D] = occupancy_grid(wf_decode_kernel<3>, 256, kCtaTilesSmem);
-        }
+    {
+        wost_status rc = once_per_device(300 + D, [&]() -> wost_status {
+            if (D == 2) {
+                WOST_CUDA(cudaFuncSetAttribute(wf_decode_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCtaTilesSmem));
+                grid_dec[D] = occupancy_grid(wf_decode_kernel<2>, 256, kCtaTilesSmem);
+            } else {
+                WOST_CUDA(cudaFuncSetAttribute(wf_decode_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCtaTilesSmem));
+                grid_dec[D] = occupancy_grid(wf_decode_kernel<3>, 256, kCtaTilesSmem);
+            }
+            return WOST_OK;
+        });
+        if (rc != WOST_OK) return rc;
     }
     // one thread per list entry (at most one per slot): the block scheduler
     // balances the uneven step costs
