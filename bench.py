@@ -68,7 +68,7 @@ WORKLOADS = {
                    dim=3, grid=1024, spp=128, eps=1e-3, maxsteps=128, train_samples=1 << 18, subset=4096,
                    ref_factor=64, batch_wpp=2,
                    step="one training batch: two walks per point of the slice (1.02M walks) + its Adam steps",
-                   l2="inputs larger than L2 (about 300 MB of BVH, 510k-walk batches); no flush"),
+                   l2="inputs larger than L2 (about 300 MB of BVH, 1.02M-walk batches); no flush"),
     "sphere3d": dict(workload="3D mixed Dirichlet/Neumann Poisson guided WoSt: icosphere 81,920 triangles displaced "
                               "by 0.15 Perlin noise, 30% Neumann cap, f = 4 Gaussians (sigma 0.1), g = 1/|x - c|, "
                               "256x256 slice z = 0 masked inside, 64 walks/point, online training after every batch "
