@@ -148,3 +148,26 @@ def test_decode_of_partial_tiles_is_row_independent(api, dim):
         assert np.array_equal(part, full[:n]), n
     o = OF.forward(pts)
     assert np.linalg.norm(full - o) / np.linalg.norm(o) < 2e-2
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_launch_order_changes_no_estimate(api, dim):
+    # guided launches hand out their points longest walks first, by the walk
+    # lengths of the scene's previous launch on as many points; with a
+    # frozen field each launch holds one walk per point, so the per-point
+    # sums add the same values in the same order whatever the order of the
+    # points: a fresh scene, the same scene again (its first launch already
+    # ordered) and a second scene must give identical estimates, and every
+    # point must get all of its walks
+    sc = wi.star_polyline(512, seed=4, neumann_frac=0.4) if dim == 2 else wi.slab_box(2)
+    S1, S2 = api.Scene(sc), api.Scene(sc)
+    F, _ = _constant_field(api, dim, sc, 70 + dim)
+    pts = _interior(sc, 300, 80 + dim)
+    kw = dict(eps=1e-3, maxsteps=256, seed=33, guided=True, field=F, guided_kernel=1)
+    m1, v1, st1 = api.solve(S1, pts, 8, **kw)
+    m2, v2, st2 = api.solve(S1, pts, 8, **kw)
+    m3, v3, st3 = api.solve(S2, pts, 8, **kw)
+    assert st1["walks"] == st2["walks"] == st3["walks"] == 8 * len(pts)
+    assert st1["walk_steps"] == st2["walk_steps"] == st3["walk_steps"]
+    assert np.array_equal(m1, m2) and np.array_equal(m1, m3)
+    assert np.array_equal(v1, v2) and np.array_equal(v1, v3)
