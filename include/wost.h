@@ -29,6 +29,11 @@
  *    when it was created; every call that uses it first checks that this
  *    device is current and otherwise returns WOST_ERR_INVALID_ARG without
  *    launching anything.
+ *  - a scene and a field each hold work buffers that their calls reuse
+ *    (per-point sums, walk slots, the launch order, training records):
+ *    calls that use the same scene or the same field must not run
+ *    concurrently (from two host threads, or on two streams before the
+ *    first has returned).  Calls on different handles are independent.
  *  - geometry is stored in FP32, per-point accumulators in FP64.
  *  - there is no CPU fallback: without a usable CUDA device every call that
  *    needs one returns WOST_ERR_CUDA.
