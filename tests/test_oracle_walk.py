@@ -103,18 +103,19 @@ def test_guided_with_c_zero_equals_plain_draw_for_draw():
             assert a["value"] == b["value"] and a["steps"] == b["steps"]
 
 
-@pytest.mark.parametrize("dim", [2, 3])
-def test_guided_mis_is_unbiased(dim):
-    # any field gives an unbiased estimator under one-sample MIS (Sec. 4.4)
+@pytest.mark.parametrize("dim,K", [(2, 8), (3, 8), (2, 16)])
+def test_guided_mis_is_unbiased(dim, K):
+    # any field gives an unbiased estimator under one-sample MIS (Sec. 4.4),
+    # whatever its lobe count
     sc = wi.half_disk(48, 12) if dim == 2 else wi.slab_box(2)
-    fld = _rand_field(sc, 2, L=4, log2T=12, base_res=4, max_res=16, w_scale=2.0)
+    fld = _rand_field(sc, 2, L=4, log2T=12, base_res=4, max_res=16, w_scale=2.0, K=K)
     n = 3000 if dim == 2 else 1500
     _check_closed_form(sc, _interior(sc, 6, 8, margin=0.1), n, guided=True, field=fld, c_mode=0)
     # guiding only (c = 1): still unbiased, the mixture has full support; a
     # mild field keeps the weights 1/(|S| alpha p_g) light-tailed enough for
     # a z-test (a sharp field is unbiased too but its variance estimate is not
     # reliable at this sample count)
-    mild = _rand_field(sc, 3, L=4, log2T=12, base_res=4, max_res=16, w_scale=0.3, grid_scale=0.1)
+    mild = _rand_field(sc, 3, L=4, log2T=12, base_res=4, max_res=16, w_scale=0.3, grid_scale=0.1, K=K)
     _check_closed_form(sc, _interior(sc, 4, 9, margin=0.1), n, guided=True, field=mild, c_mode=1,
                        c_fixed=1.0)
 
