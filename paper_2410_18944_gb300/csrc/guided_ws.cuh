@@ -32,6 +32,11 @@
 // will not come.
 // Every wait is bounded; a give-up sets the error word and ends the loops.
 //
+// Lobe capacity KM: the decoded rows hold the internal output layout of 8
+// lobes (48 outputs, written over the dead hidden tile) or, for fields of
+// 9..16 lobes, of 16 (96 outputs: 128 TMEM columns per tile buffer and a
+// shared-memory region of their own); single-scene launches only.
+//
 // Multi-scene tiles: each row records the job of its walk.  The server runs
 // the three-layer chain once per distinct job in the tile, with that job's
 // weights (a small cache of weight images in shared memory, refilled from

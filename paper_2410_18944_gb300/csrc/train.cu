@@ -7,7 +7,9 @@
 // Eq. one_sample_kld for Theta and Eq. one_sample_sp for c.  The mean over
 // records is back-propagated through the MLP and scattered onto the hash grid.
 //
-// One fused persistent kernel, two 128-record tiles per CTA (256 threads):
+// One fused persistent kernel, two 128-record tiles per CTA (256 threads;
+// one tile of 128 threads for fields of 9..16 lobes, whose 96 outputs widen
+// the gradient tile and the TMEM columns beyond two tiles per SM):
 //   forward recomputation (3 tcgen05 MMAs) -> per-thread loss and d raw ->
 //   dH2 = dY W3, dZ2 = dH2 * [H2 > 0] -> dH1 = dZ2 W2 -> dZ1 -> dX = dZ1 W1
 //   -> hash-grid scatter-add (FP32 atomics); the weight gradients
